@@ -1,0 +1,196 @@
+/*
+ * wd.h -- C ABI of a GB300 (sm_103a) mixed-precision Wilson-Dirac solver.
+ *
+ * The library solves D_W xi = eta (Eq. 3) for the Wilson matrix of Eq. 1,
+ *   D_W = 1 - kappa * H,
+ *   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                       + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ],
+ * through the even-odd system of Eqs. 4-5 (A = 1 - kappa^2 H_eo H_oe on even
+ * sites), with the FP64 iterative refinement of Algorithms 1-2 around the
+ * rescaled low-precision BiCGStab of Algorithms 3-4.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - dims = {Lx, Ly, Lz, Lt}; every extent even and >= 2.
+ * - Lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t)); parity of a site
+ *   is (x+y+z+t) mod 2, 0 = even.
+ * - Dirac matrices: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1..3),
+ *   gamma_4 = diag(1, 1, -1, -1); this is the representation whose
+ *   (1 - gamma_1) is printed in Eq. 2.
+ * - Boundary phases bc[mu] in {+1, -1} multiply hops that wrap around the
+ *   lattice in direction mu; default {1, 1, 1, -1} (antiperiodic in time).
+ * - Host / "lexicographic" layouts, all float64 with (re, im) innermost:
+ *     gauge  U[mu][s][a][b][2] = (U_mu(x_s))_ab,  mu = 0..3 is x, y, z, t;
+ *     vector psi[s][spin][colour][2] (24 doubles per site).
+ * - Packed layouts (device only, produced by wd_pack / consumed by
+ *   wd_unpack): one parity of a vector is V/2 sites of 24 reals in the
+ *   precision's storage type, stored as 16-byte units with the site index
+ *   fastest: unit u of site h sits at byte 16 * (u * V/2 + h). Site h of
+ *   parity p is the lexicographic site 2h or 2h+1 whose parity is p.
+ *   wd_vector_bytes() gives the size of one parity vector; a "full" packed
+ *   vector is the even parity followed by the odd parity.
+ * - All device work is enqueued on the caller's CUDA stream (a
+ *   cudaStream_t passed as void*, NULL = legacy default stream). Entry
+ *   points that return a result synchronize that stream only when stated.
+ * - Return value: a wd_status code. No C++ exception crosses this ABI. The
+ *   text of the last failure of a handle is in wd_last_error().
+ * - Ownership: the library copies every input; callers keep their buffers.
+ *   The handle owns its device workspaces (allocated on first use, freed
+ *   by wd_destroy).
+ * - Thread safety: one handle must not be used from two host threads at once.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_handle wd_handle;
+
+/* Status codes. */
+enum wd_status {
+    WD_OK = 0,
+    WD_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or state                      */
+    WD_ERR_CUDA = 2,          /* a CUDA runtime call failed                            */
+    WD_ERR_NOT_SU3 = 3,       /* 12-real links requested but U is not in SU(3)         */
+    WD_ERR_NOT_CONVERGED = 4, /* iteration caps reached; best iterate returned         */
+    WD_ERR_BREAKDOWN = 5,     /* (r*, v) = 0 or (t, t) = 0 in BiCGStab                 */
+    WD_ERR_NONFINITE = 6,     /* a scalar of the recurrence became Inf or NaN          */
+    WD_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                    */
+    WD_ERR_NO_GAUGE = 8       /* wd_set_gauge has not been called                      */
+};
+
+/* Storage precisions of packed vectors and links. Arithmetic is FP32 for
+ * FP32/FP16/BF16 storage and FP64 for FP64 storage. */
+enum wd_prec { WD_FP64 = 0, WD_FP32 = 1, WD_FP16 = 2, WD_BF16 = 3 };
+
+/* Link formats: 18 reals (full 3x3) or 12 reals (two rows; the third row is
+ * rebuilt as the complex conjugate of the cross product of the first two,
+ * exact for SU(3)). */
+enum wd_recon { WD_RECON_12 = 12, WD_RECON_18 = 18 };
+
+/* Operators of wd_apply (Eq. 1 and Eq. 4). */
+enum wd_op {
+    WD_OP_HOP_EO = 0, /* out(even) = H_eo in(odd)                                   */
+    WD_OP_HOP_OE = 1, /* out(odd)  = H_oe in(even)                                  */
+    WD_OP_EO_A = 2,   /* out(even) = in - kappa^2 H_eo H_oe in   (bracket of Eq. 4) */
+    WD_OP_FULL = 3    /* out(full) = D_W in (full packed vectors, Eq. 1)            */
+};
+
+/* Where a caller's buffer lives. */
+enum wd_where { WD_HOST = 0, WD_DEVICE = 1 };
+
+/* Solver schemes (Sec. 3 and Table 2). */
+enum wd_scheme {
+    WD_FP64_BICGSTAB = 0,     /* BiCGStab (Alg. 3 with gamma = 1) entirely in FP64       */
+    WD_MIXED_FP32 = 1,        /* Alg. 1 refinement, FP32 inner BiCGStab without rescaling */
+    WD_MIXED_FP16_PLAIN = 2,  /* Alg. 1 refinement, FP16 inner without rescaling          */
+    WD_MIXED_FP16 = 3,        /* Alg. 2 refinement, FP16 inner Alg. 3 / Alg. 4            */
+    WD_MIXED_BF16 = 4         /* as WD_MIXED_FP16 with BF16 storage (Sec. 6 outlook)      */
+};
+
+/* Knobs of Algorithms 1-4. wd_solve_params_default() fills the values a
+ * scheme uses by default. */
+typedef struct wd_solve_params {
+    double s;             /* Alg. 2: norm of the rescaled outer residual y (Alg. 1: 1)      */
+    double sigma;         /* Alg. 3: norm of the inner residual after rescaling; 0 = none  */
+    double sigma_lambda;  /* Alg. 4: norm of the rescaled inner solution                    */
+    double inner_eps;     /* inner stop: |r|/gamma' <= inner_eps * |y~| (eps, not eps^2)    */
+    double omega0;        /* omega_0 of the BiCGStab prescription (0.7)                     */
+    int recalc_gamma;     /* gamma := |r_stored| / g  instead of sigma / g                   */
+    int rescale_x;        /* Alg. 4 (solution rescaling)                                     */
+    int use_shat;         /* Alg. 2: correct with s^ = |single(y~)| instead of s             */
+    int x_is_guess;       /* x holds an initial guess (restart from a previous solution)    */
+    int max_outer;        /* cap on refinement trips                                         */
+    int max_inner;        /* cap on low-precision matrix-vector products per inner solve    */
+    int recon;            /* link format of the inner operator: 12 or 18                     */
+    int ftz;              /* flush subnormal low-precision values to zero on store           */
+    int iters_per_sync;   /* inner iterations captured per CUDA-graph launch                 */
+} wd_solve_params;
+
+/* Counters of one solve. */
+typedef struct wd_solve_stats {
+    int status;                /* wd_status of the solve                                 */
+    int outer_iterations;      /* refinement trips (Alg. 1/2 loop bodies)                */
+    int inner_iterations;      /* BiCGStab iterations summed over trips                  */
+    int inner_matvecs;         /* low-precision applications of A (2 per iteration)     */
+    int outer_matvecs;         /* FP64 applications of A (true residuals)                */
+    double true_residual;      /* |eta - D_W xi| / |eta|, computed in FP64 on the GPU    */
+    double outer_residual;     /* last |b^ - A xi_e| / |eta| of the refinement           */
+    double elapsed_ms;         /* device time of the whole solve (CUDA events)           */
+    long long first_inner_nonzeros; /* nonzero reals of the first low-precision input    */
+    long long kernel_launches; /* device kernels this call launched (graph nodes included) */
+} wd_solve_stats;
+
+/* Create a lattice handle. dims: 4 even extents >= 2, Lx*Ly*Lz*Lt/2 < 2^31.
+ * kappa: hopping parameter of Eq. 1. bc: 4 boundary phases in {+1,-1}, or
+ * NULL for {1,1,1,-1}. On success *out owns no device memory yet. */
+int wd_create(const int dims[4], double kappa, const int bc[4], wd_handle** out);
+
+/* Release the handle and all its device memory (synchronizes the device). */
+int wd_destroy(wd_handle* h);
+
+/* Load the gauge field U (Sec. 2, links U_mu(x) on x -> x+mu). U is in the
+ * host layout above, 4*V*18 doubles, host or device memory as `where` says.
+ * The library keeps an FP64 copy on the device and builds each packed link
+ * format on first use. Synchronizes the default stream. */
+int wd_set_gauge(wd_handle* h, const double* U, int where);
+
+/* Largest |U U^+ - 1| entry and |det U - 1| over all links of the loaded
+ * gauge field (FP64). 12-real formats are refused when either exceeds 1e-6. */
+int wd_gauge_unitarity(wd_handle* h, double* max_unitarity_dev, double* max_det_dev);
+
+/* Bytes of one packed parity vector in precision `prec` (24 * V/2 reals). */
+size_t wd_vector_bytes(const wd_handle* h, int prec);
+
+/* Pack the sites of parity `parity` of the device FP64 lexicographic vector
+ * `lex` (24*V doubles) into the device buffer `packed` (wd_vector_bytes). */
+int wd_pack(wd_handle* h, int prec, int parity, const double* lex, void* packed, void* stream);
+
+/* Scatter the packed parity vector back into the device FP64 lexicographic
+ * vector `lex`; sites of the other parity are left untouched. */
+int wd_unpack(wd_handle* h, int prec, int parity, const void* packed, double* lex, void* stream);
+
+/* Apply an operator (enum wd_op) in storage precision `prec` with link
+ * format `recon` to the packed device vector `in`, writing packed `out`
+ * (in and out must not overlap). Arithmetic as in enum wd_prec. */
+int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* out, void* stream);
+
+/* Fill `p` with the defaults of `scheme` (Table 2 rows; s = 128, sigma = 64
+ * for WD_MIXED_FP16). */
+int wd_solve_params_default(int scheme, wd_solve_params* p);
+
+/* Solve D_W x = b to |b - D_W x| <= tol |b| (Alg. 2 + Alg. 3/4 around the
+ * even-odd system, Eqs. 4-5). b and x are full-lattice FP64 vectors in the
+ * host layout, in host or device memory (detected per pointer; host buffers
+ * are copied in and out inside the call). params may be NULL (defaults of
+ * the scheme); stats may be NULL. Synchronizes `stream` once per refinement
+ * trip to read the outer residual norm, and at the end.
+ * Returns WD_OK, WD_ERR_NOT_CONVERGED (x holds the best iterate),
+ * WD_ERR_BREAKDOWN, WD_ERR_NONFINITE, or an argument / CUDA error. */
+int wd_solve(wd_handle* h, const double* b, double* x, double tol, int scheme,
+             const wd_solve_params* params, wd_solve_stats* stats, void* stream);
+
+/* Solve several right-hand sides on several lattices in one batched launch
+ * chain. For lattice i (0 <= i < n), nrhs[i] sources b[i] and solutions x[i]
+ * are stored back to back (nrhs[i] full-lattice vectors each, device memory).
+ * Links are read once per site for all right-hand sides of a lattice.
+ * per_rhs_stats (optional) receives sum(nrhs) entries in order. */
+int wd_solve_batch(int n, wd_handle* const* h, const int* nrhs, const double* const* b,
+                   double* const* x, double tol, int scheme, const wd_solve_params* params,
+                   wd_solve_stats* per_rhs_stats, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* wd_status_string(int status);
+
+/* Text of the last error raised on handle h (static storage owned by h). */
+const char* wd_last_error(const wd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WD_H */

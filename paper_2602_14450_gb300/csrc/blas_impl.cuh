@@ -1,0 +1,297 @@
+// Fused vector kernels of the rescaled BiCGStab (Alg. 3/4) and of the
+// refinement loop (Alg. 1/2), plus layout conversions. Every kernel streams
+// packed parity vectors unit by unit; reductions keep per-thread partial
+// sums in the arithmetic type (FP32 for low-precision storage, as in the
+// paper's Fig. 3) and combine threads, blocks and the grid in FP64.
+#pragma once
+
+#include "common.cuh"
+
+namespace wd {
+
+// out = (a + ib) * v for one complex element pair
+template <typename C>
+__device__ __forceinline__ void cscale_add(C& or_, C& oi, C ar, C ai, C vr, C vi) {
+    or_ += ar * vr - ai * vi;
+    oi += ar * vi + ai * vr;
+}
+
+#define GRID_STRIDE(h, n) for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < (n); h += gridDim.x * blockDim.x)
+
+// p := r (first iteration) or cP p - cV v + r
+template <typename T>
+__global__ void __launch_bounds__(256) k_pupdate(int n, uint4* p, const uint4* v, const uint4* r, const SolverState* st) {
+    typedef typename Unit<T>::C C;
+    if (solve_done(st)) return;
+    const bool first = st->first;
+    const C pr = (C)st->cP[0], pi = (C)st->cP[1], vr = (C)st->cV[0], vi = (C)st->cV[1];
+    GRID_STRIDE(h, n) {
+        C rr[24], o[24];
+        load_spinor<T>(r, n, h, rr);
+        if (first) {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) o[i] = rr[i];
+        } else {
+            C pp[24], vv[24];
+            load_spinor<T>(p, n, h, pp);
+            load_spinor<T>(v, n, h, vv);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                C a = rr[2 * i], b = rr[2 * i + 1];
+                cscale_add(a, b, pr, pi, pp[2 * i], pp[2 * i + 1]);
+                cscale_add(a, b, -vr, -vi, vv[2 * i], vv[2 * i + 1]);
+                o[2 * i] = a;
+                o[2 * i + 1] = b;
+            }
+        }
+        store_spinor<T>(p, n, h, o);
+    }
+}
+
+// r := r - alpha v
+template <typename T>
+__global__ void __launch_bounds__(256) k_supdate(int n, uint4* r, const uint4* v, const SolverState* st) {
+    typedef typename Unit<T>::C C;
+    if (solve_done(st)) return;
+    const C ar = (C)-st->alpha[0], ai = (C)-st->alpha[1];
+    GRID_STRIDE(h, n) {
+        C rr[24], vv[24];
+        load_spinor<T>(r, n, h, rr);
+        load_spinor<T>(v, n, h, vv);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], ar, ai, vv[2 * i], vv[2 * i + 1]);
+        store_spinor<T>(r, n, h, rr);
+    }
+}
+
+// x := x + cXr r + cXp p  (x := cXr r + cXp p on the first iteration)
+// r := r - omega t
+// sums: |r|^2, |x|^2, (r*, r) [the last only when WITH_RS]
+template <typename T, bool WITH_RS>
+__global__ void __launch_bounds__(256) k_xr(int n, uint4* x, uint4* r, const uint4* p, const uint4* t,
+                                            const uint4* rstar, SolverState* st, RedCtx rc) {
+    typedef typename Unit<T>::C C;
+    if (solve_done(st)) return;
+    const bool first = st->first;
+    const C xr_r = (C)st->cXr[0], xr_i = (C)st->cXr[1], xp_r = (C)st->cXp[0], xp_i = (C)st->cXp[1];
+    const C om_r = (C)-st->omega[0], om_i = (C)-st->omega[1];
+    C s_r2 = 0, s_x2 = 0, s_re = 0, s_im = 0;
+    GRID_STRIDE(h, n) {
+        C rr[24], pp[24], xx[24], tt[24];
+        load_spinor<T>(r, n, h, rr);
+        load_spinor<T>(p, n, h, pp);
+        if (first) {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) xx[i] = 0;
+        } else {
+            load_spinor<T>(x, n, h, xx);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            cscale_add(xx[2 * i], xx[2 * i + 1], xr_r, xr_i, rr[2 * i], rr[2 * i + 1]);
+            cscale_add(xx[2 * i], xx[2 * i + 1], xp_r, xp_i, pp[2 * i], pp[2 * i + 1]);
+        }
+        store_spinor<T>(x, n, h, xx);
+        load_spinor<T>(t, n, h, tt);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, tt[2 * i], tt[2 * i + 1]);
+        store_spinor<T>(r, n, h, rr);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            s_r2 += rr[i] * rr[i];
+            s_x2 += xx[i] * xx[i];
+        }
+        if constexpr (WITH_RS) {
+            C rs[24];
+            load_spinor<T>(rstar, n, h, rs);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                s_re += rs[2 * i] * rr[2 * i] + rs[2 * i + 1] * rr[2 * i + 1];
+                s_im += rs[2 * i] * rr[2 * i + 1] - rs[2 * i + 1] * rr[2 * i];
+            }
+        }
+    }
+    double v[4] = {(double)s_r2, (double)s_x2, (double)s_re, (double)s_im};
+    grid_reduce<4>(v, rc);
+}
+
+// r := (sigma / g) r, and x := lambda x when rescaling the solution (Alg. 4)
+// sums: |r|^2, (r*, r)
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale(int n, uint4* r, uint4* x, const uint4* rstar, SolverState* st, RedCtx rc) {
+    typedef typename Unit<T>::C C;
+    if (solve_done(st)) return;
+    const C gs = (C)st->gam_tmp;
+    const bool resx = st->rescale_x;
+    const C lam = (C)st->lam;
+    C s_r2 = 0, s_re = 0, s_im = 0;
+    GRID_STRIDE(h, n) {
+        C rr[24], rs[24];
+        load_spinor<T>(r, n, h, rr);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) rr[i] *= gs;
+        store_spinor<T>(r, n, h, rr);
+        load_spinor<T>(rstar, n, h, rs);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            s_r2 += rr[2 * i] * rr[2 * i] + rr[2 * i + 1] * rr[2 * i + 1];
+            s_re += rs[2 * i] * rr[2 * i] + rs[2 * i + 1] * rr[2 * i + 1];
+            s_im += rs[2 * i] * rr[2 * i + 1] - rs[2 * i + 1] * rr[2 * i];
+        }
+        if (resx) {
+            C xx[24];
+            load_spinor<T>(x, n, h, xx);
+#pragma unroll
+            for (int i = 0; i < 24; ++i) xx[i] *= lam;
+            store_spinor<T>(x, n, h, xx);
+        }
+    }
+    double v[3] = {(double)s_r2, (double)s_re, (double)s_im};
+    grid_reduce<3>(v, rc);
+}
+
+// Rescale the FP64 outer residual and demote it (Alg. 2, first lines):
+// y~ = low_prec((s / |r|) r) written to r and r*; sums |single(y~)|^2 and the
+// count of nonzero reals. The product is formed in FP64 and rounded once.
+template <typename T>
+__device__ __forceinline__ T from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <typename T>
+__device__ __forceinline__ double to_double(T v);
+template <> __device__ __forceinline__ double to_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_double<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double to_double<__half>(__half v) { return (double)__half2float(v); }
+template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// Element e (0..23) of site h of a packed vector of T, as a typed pointer.
+template <typename T>
+__device__ __forceinline__ T* elem_ptr(uint4* base, int stride, int h, int e) {
+    constexpr int N = Unit<T>::N;
+    return reinterpret_cast<T*>(base + (size_t)(e / N) * stride + h) + (e % N);
+}
+template <typename T>
+__device__ __forceinline__ const T* elem_ptr(const uint4* base, int stride, int h, int e) {
+    constexpr int N = Unit<T>::N;
+    return reinterpret_cast<const T*>(base + (size_t)(e / N) * stride + h) + (e % N);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rescale_in(int n, const uint4* r64, uint4* r, uint4* rstar, int ftz,
+                                                    SolverState* st, RedCtx rc) {
+    typedef typename Unit<T>::C C;
+    constexpr int N = Unit<T>::N;
+    const double f = st->s / st->rnorm;
+    C s_n2 = 0;
+    double nz = 0;
+    GRID_STRIDE(h, n) {
+        double src[24];
+        load_spinor<double>(r64, n, h, src);
+        alignas(16) T y[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            T v = from_double<T>(f * src[i]);
+            double dv = to_double<T>(v);
+            if (ftz && fabs(dv) < (sizeof(T) == 2 ? 6.103515625e-05 : 1.1754943508222875e-38)) {
+                v = from_double<T>(0.0);
+                dv = 0.0;
+            }
+            y[i] = v;
+            s_n2 += (C)(dv * dv);
+            nz += dv != 0.0 ? 1.0 : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 24 / N; ++u) {
+            uint4 w = *reinterpret_cast<const uint4*>(&y[u * N]);
+            r[(size_t)u * n + h] = w;
+            rstar[(size_t)u * n + h] = w;
+        }
+    }
+    double v[2] = {(double)s_n2, nz};
+    grid_reduce<2>(v, rc);
+}
+
+// x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 2 correction; Alg. 1: s^ -> s)
+template <typename T>
+__global__ void __launch_bounds__(256) k_correct(int n, uint4* x64, const uint4* xt, const SolverState* st) {
+    const double f = st->rnorm / (st->use_shat ? st->shat : st->s) / st->lambda_p;
+    GRID_STRIDE(h, n) {
+#pragma unroll
+        for (int e = 0; e < 24; ++e) {
+            double* xp = elem_ptr<double>(x64, n, h, e);
+            *xp += f * to_double<T>(*elem_ptr<T>(xt, n, h, e));
+        }
+    }
+}
+
+// sum |v|^2 over a packed vector; stage as given (ST_ACC / ST_ACC_SET / ST_OUTER)
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm2(int n, const uint4* v, RedCtx rc) {
+    typedef typename Unit<T>::C C;
+    C s = 0;
+    GRID_STRIDE(h, n) {
+        C a[24];
+        load_spinor<T>(v, n, h, a);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) s += a[i] * a[i];
+    }
+    double d[1] = {(double)s};
+    grid_reduce<1>(d, rc);
+}
+
+// lex FP64 (24 doubles per site) -> packed parity vector of T
+template <typename T>
+__global__ void k_pack(Geom g, int parity, const double* lex, uint4* out) {
+    GRID_STRIDE(h, g.Vh) {
+        const int s = lex_of(g, parity, h);
+#pragma unroll
+        for (int e = 0; e < 24; ++e) *elem_ptr<T>(out, g.Vh, h, e) = from_double<T>(lex[(size_t)s * 24 + e]);
+    }
+}
+
+template <typename T>
+__global__ void k_unpack(Geom g, int parity, const uint4* in, double* lex) {
+    GRID_STRIDE(h, g.Vh) {
+        const int s = lex_of(g, parity, h);
+#pragma unroll
+        for (int e = 0; e < 24; ++e) lex[(size_t)s * 24 + e] = to_double<T>(*elem_ptr<T>(in, g.Vh, h, e));
+    }
+}
+
+// Gathered links of output parity p (see hop_impl.cuh) from FP64 lex links.
+template <typename T, int R>
+__global__ void k_build_links(Geom g, int parity, const double* U, uint4* out) {
+    constexpr int N = Unit<T>::N;
+    const int V = 2 * g.Vh;
+    GRID_STRIDE(h, g.Vh) {
+        const int s = lex_of(g, parity, h);
+        int c[4];
+        c[0] = s % g.L[0];
+        c[1] = (s / g.L[0]) % g.L[1];
+        c[2] = (s / (g.L[0] * g.L[1])) % g.L[2];
+        c[3] = s / (g.L[0] * g.L[1] * g.L[2]);
+        for (int mu = 0; mu < 4; ++mu) {
+            int cm[4] = {c[0], c[1], c[2], c[3]};
+            cm[mu] = (c[mu] + g.L[mu] - 1) % g.L[mu];
+            const int sm = cm[0] + g.L[0] * (cm[1] + g.L[1] * (cm[2] + g.L[2] * cm[3]));
+            const double* uf = U + ((size_t)mu * V + s) * 18;
+            const double* ub = U + ((size_t)mu * V + sm) * 18;
+            for (int e = 0; e < R; ++e) {
+                // forward: U_mu(x)[a][b]; backward: (U_mu(x-mu)^+)[a][b] = conj(U_mu(x-mu)[b][a])
+                const int a = e / 6, b = (e % 6) / 2, im = e & 1;
+                const double vf = uf[e];
+                const double vb = im ? -ub[2 * (3 * b + a) + 1] : ub[2 * (3 * b + a)];
+                const int ef = (2 * mu) * R + e, eb = (2 * mu + 1) * R + e;
+                reinterpret_cast<T*>(out + (size_t)(ef / N) * g.Vh + h)[ef % N] = from_double<T>(vf);
+                reinterpret_cast<T*>(out + (size_t)(eb / N) * g.Vh + h)[eb % N] = from_double<T>(vb);
+            }
+        }
+    }
+}
+
+#undef GRID_STRIDE
+
+}  // namespace wd

@@ -1,0 +1,423 @@
+// Shared device-side definitions of the Wilson-Dirac solver library.
+//
+// Storage: every packed field (spinor parity vector, gathered links) is an
+// array of 16-byte units with the site index fastest: unit u of site h is at
+// units[u * stride + h]. A unit holds 2 doubles, 4 floats, or 8 halves /
+// bfloat16s. Arithmetic type C is float for FP32/FP16/BF16 storage and
+// double for FP64 storage.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wd {
+
+// ---------------------------------------------------------------- storage ---
+
+template <typename T> struct Unit;
+
+template <> struct Unit<double> {
+    typedef double C;
+    static constexpr int N = 2;
+    __device__ __forceinline__ static C get(const uint4& u, int i) {
+        return i == 0 ? __hiloint2double((int)u.y, (int)u.x) : __hiloint2double((int)u.w, (int)u.z);
+    }
+    __device__ __forceinline__ static uint4 put(const C* v) {
+        uint4 u;
+        u.x = (unsigned)__double2loint(v[0]);
+        u.y = (unsigned)__double2hiint(v[0]);
+        u.z = (unsigned)__double2loint(v[1]);
+        u.w = (unsigned)__double2hiint(v[1]);
+        return u;
+    }
+};
+
+template <> struct Unit<float> {
+    typedef float C;
+    static constexpr int N = 4;
+    __device__ __forceinline__ static C get(const uint4& u, int i) {
+        unsigned w = i == 0 ? u.x : i == 1 ? u.y : i == 2 ? u.z : u.w;
+        return __uint_as_float(w);
+    }
+    __device__ __forceinline__ static uint4 put(const C* v) {
+        return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+    }
+};
+
+__device__ __forceinline__ unsigned word_of(const uint4& u, int w) {
+    return w == 0 ? u.x : w == 1 ? u.y : w == 2 ? u.z : u.w;
+}
+
+template <> struct Unit<__half> {
+    typedef float C;
+    static constexpr int N = 8;
+    __device__ __forceinline__ static C get(const uint4& u, int i) {
+        unsigned w = word_of(u, i >> 1);
+        __half2 h = *reinterpret_cast<__half2*>(&w);
+        return (i & 1) ? __high2float(h) : __low2float(h);
+    }
+    __device__ __forceinline__ static uint4 put(const C* v) {
+        uint4 u;
+        __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+        __half2 c = __floats2half2_rn(v[4], v[5]), d = __floats2half2_rn(v[6], v[7]);
+        u.x = *reinterpret_cast<unsigned*>(&a);
+        u.y = *reinterpret_cast<unsigned*>(&b);
+        u.z = *reinterpret_cast<unsigned*>(&c);
+        u.w = *reinterpret_cast<unsigned*>(&d);
+        return u;
+    }
+};
+
+template <> struct Unit<__nv_bfloat16> {
+    typedef float C;
+    static constexpr int N = 8;
+    __device__ __forceinline__ static C get(const uint4& u, int i) {
+        unsigned w = word_of(u, i >> 1);
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+        return (i & 1) ? __high2float(h) : __low2float(h);
+    }
+    __device__ __forceinline__ static uint4 put(const C* v) {
+        uint4 u;
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 c = __floats2bfloat162_rn(v[4], v[5]), d = __floats2bfloat162_rn(v[6], v[7]);
+        u.x = *reinterpret_cast<unsigned*>(&a);
+        u.y = *reinterpret_cast<unsigned*>(&b);
+        u.z = *reinterpret_cast<unsigned*>(&c);
+        u.w = *reinterpret_cast<unsigned*>(&d);
+        return u;
+    }
+};
+
+// Units of one site of a spinor (24 reals).
+template <typename T> struct Spinor {
+    static constexpr int UNITS = 24 / Unit<T>::N;
+};
+
+// Load the 24 reals of site h (order: spin, colour, re/im).
+template <typename T>
+__device__ __forceinline__ void load_spinor(const uint4* __restrict__ v, int stride, int h,
+                                            typename Unit<T>::C (&s)[24]) {
+    constexpr int N = Unit<T>::N;
+#pragma unroll
+    for (int u = 0; u < 24 / N; ++u) {
+        uint4 w = __ldg(v + (size_t)u * stride + h);
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[u * N + i] = Unit<T>::get(w, i);
+    }
+}
+
+// Load as stored by a previous kernel of the same launch chain (coherent load).
+template <typename T>
+__device__ __forceinline__ void load_spinor_cg(const uint4* v, int stride, int h, typename Unit<T>::C (&s)[24]) {
+    constexpr int N = Unit<T>::N;
+#pragma unroll
+    for (int u = 0; u < 24 / N; ++u) {
+        uint4 w = __ldcg(v + (size_t)u * stride + h);
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[u * N + i] = Unit<T>::get(w, i);
+    }
+}
+
+// Round to storage and write; `s` is overwritten with the stored values so
+// that reductions see exactly what later kernels will read.
+template <typename T>
+__device__ __forceinline__ void store_spinor(uint4* v, int stride, int h, typename Unit<T>::C (&s)[24]) {
+    constexpr int N = Unit<T>::N;
+#pragma unroll
+    for (int u = 0; u < 24 / N; ++u) {
+        uint4 w = Unit<T>::put(&s[u * N]);
+        v[(size_t)u * stride + h] = w;
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[u * N + i] = Unit<T>::get(w, i);
+    }
+}
+
+// --------------------------------------------------------------- geometry ---
+
+struct Geom {
+    int L[4];    // Lx, Ly, Lz, Lt
+    int Lxh;     // Lx / 2
+    int Vh;      // V / 2 (sites per parity)
+    int bc[4];   // boundary phases, +1 or -1
+};
+
+// Lexicographic index of site h on parity p.
+__device__ __forceinline__ int lex_of(const Geom& g, int p, int h) {
+    int row = h / g.Lxh;
+    int xh = h - row * g.Lxh;
+    int y = row % g.L[1];
+    int r2 = row / g.L[1];
+    int z = r2 % g.L[2];
+    int t = r2 / g.L[2];
+    int x = 2 * xh + ((p + y + z + t) & 1);
+    return x + g.L[0] * row;
+}
+
+// ---------------------------------------------------------------- complex ---
+
+template <typename C> struct cpx {
+    C re, im;
+};
+template <typename C> __device__ __forceinline__ cpx<C> mk(C a, C b) { cpx<C> z; z.re = a; z.im = b; return z; }
+
+// -------------------------------------------------------- solver scalars ---
+
+// FP64 scalar state of one right-hand side (Alg. 3/4 and the Alg. 1/2 loop).
+// Complex scalars are (re, im) pairs.
+struct SolverState {
+    double rho[2], rho_p[2];        // (r*, r) and rho'
+    double alpha[2], alpha_p[2];    // alpha, alpha'
+    double omega[2], omega_p[2];    // omega, omega'
+    double cP[2], cV[2];            // p := cP p - cV v + r   (beta*gamma, beta*gamma*omega')
+    double cXr[2], cXp[2];          // x += cXr r + cXp p     (lambda'/gamma' * (omega, alpha))
+    double gamma_p;                 // gamma'
+    double lambda_p;                // lambda'
+    double lam;                     // lambda of this iteration (Alg. 4)
+    double g;                       // |r| before rescaling
+    double gam_tmp;                 // sigma / g, the factor applied to r
+    double bnorm;                   // |b| of the inner system
+    double res;                     // |r| / gamma'
+    double sigma, sigma_lambda, eps, omega0;
+    int recalc, rescale_x, max_matvecs, scale_pass;
+    int iter, matvecs, first, done, status;
+    // refinement (outer) scalars
+    double rnorm;                   // |b^ - A x| of the FP64 outer residual
+    double shat;                    // |single(y~)|
+    double s;                       // target norm of y
+    int use_shat;
+    double acc;                     // accumulator for multi-kernel norms
+    long long nonzeros;             // nonzero reals of the last rescaled input
+};
+
+enum Stage {
+    ST_NONE = 0,
+    ST_INIT = 1,     // sums: |y~|^2, nonzeros      -> start an inner solve
+    ST_ALPHA = 2,    // sums: (r*, v)               -> alpha
+    ST_OMEGA = 3,    // sums: (t,s), (t,t), (s,s)   -> omega (omega_0 prescription)
+    ST_RNORM = 4,    // sums: |r|^2, |x|^2, (r*, r) -> g, sigma/g, lambda (or end of iteration)
+    ST_END = 5,      // sums: |r_st|^2, (r*, r_st)  -> gamma, beta, convergence
+    ST_OUTER = 6,    // sums: |r64|^2               -> outer residual norm
+    ST_ACC = 7,      // sums: x                     -> acc += x
+    ST_ACC_SET = 8   // sums: x                     -> acc  = x
+};
+
+__device__ __forceinline__ bool finite2(const double* z) { return isfinite(z[0]) && isfinite(z[1]); }
+
+__device__ __forceinline__ void cdiv(const double* a, const double* b, double* out) {
+    double d = b[0] * b[0] + b[1] * b[1];
+    double re = (a[0] * b[0] + a[1] * b[1]) / d;
+    double im = (a[1] * b[0] - a[0] * b[1]) / d;
+    out[0] = re;
+    out[1] = im;
+}
+__device__ __forceinline__ void cmul(const double* a, const double* b, double* out) {
+    double re = a[0] * b[0] - a[1] * b[1];
+    double im = a[0] * b[1] + a[1] * b[0];
+    out[0] = re;
+    out[1] = im;
+}
+
+// Status codes (mirror enum wd_status of wd.h).
+enum { S_OK = 0, S_NOT_CONVERGED = 4, S_BREAKDOWN = 5, S_NONFINITE = 6 };
+
+__device__ inline void stop(SolverState* st, int status) {
+    st->done = 1;
+    if (st->status == S_OK) st->status = status;
+}
+
+// End of a BiCGStab iteration (Alg. 3 last lines): gamma known, r stored.
+// rn2 = |r_stored|^2, rs = (r*, r_stored).
+__device__ inline void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
+    double rho_new[2] = {rs[0], rs[1]};
+    // rho' = gamma * rho, gamma' *= gamma, alpha' = alpha, omega' = omega
+    st->rho_p[0] = gamma * st->rho[0];
+    st->rho_p[1] = gamma * st->rho[1];
+    st->gamma_p *= gamma;
+    st->alpha_p[0] = st->alpha[0]; st->alpha_p[1] = st->alpha[1];
+    st->omega_p[0] = st->omega[0]; st->omega_p[1] = st->omega[1];
+    if (st->rescale_x) st->lambda_p *= st->lam;
+    st->rho[0] = rho_new[0];
+    st->rho[1] = rho_new[1];
+    // beta = rho alpha' / (rho' omega'); p-update folds the gamma of p and v.
+    double num[2], den[2], beta[2];
+    cmul(st->rho, st->alpha_p, num);
+    cmul(st->rho_p, st->omega_p, den);
+    cdiv(num, den, beta);
+    st->cP[0] = gamma * beta[0];
+    st->cP[1] = gamma * beta[1];
+    cmul(st->cP, st->omega_p, st->cV);
+    st->iter += 1;
+    st->matvecs += 2;
+    st->first = 0;
+    st->res = sqrt(rn2) / st->gamma_p;
+    if (!(isfinite(st->res) && finite2(st->cP) && finite2(st->cV) && isfinite(st->gamma_p))) {
+        stop(st, S_NONFINITE);
+        return;
+    }
+    if (st->res <= st->eps * st->bnorm) { stop(st, S_OK); return; }
+    if (st->matvecs >= st->max_matvecs) { stop(st, S_NOT_CONVERGED); return; }
+    if (den[0] == 0.0 && den[1] == 0.0) stop(st, S_BREAKDOWN);
+}
+
+// Scalar work done by the last block of a reducing kernel, one thread.
+__device__ inline void run_stage(int stage, const double* s, SolverState* st) {
+    switch (stage) {
+    case ST_INIT: {
+        double n2 = s[0];
+        st->shat = sqrt(n2);
+        st->nonzeros = (long long)s[1];
+        st->bnorm = st->use_shat ? st->shat : st->s;
+        // Alg. 3 start: r = r* = y~, p = v = 0, rho' = |r|^2, omega' = alpha' = gamma' = 1
+        st->rho[0] = n2; st->rho[1] = 0;
+        st->rho_p[0] = n2; st->rho_p[1] = 0;
+        st->alpha_p[0] = 1; st->alpha_p[1] = 0;
+        st->omega_p[0] = 1; st->omega_p[1] = 0;
+        st->cP[0] = st->cP[1] = st->cV[0] = st->cV[1] = 0;
+        st->gamma_p = 1;
+        st->lambda_p = 1;
+        st->lam = 1;
+        st->iter = 0;
+        st->matvecs = 0;
+        st->first = 1;
+        st->done = 0;
+        st->status = S_OK;
+        st->res = st->shat;
+        if (!(n2 > 0) || !isfinite(n2)) stop(st, isfinite(n2) ? S_OK : S_NONFINITE);
+        break;
+    }
+    case ST_ALPHA: {
+        double rv[2] = {s[0], s[1]};
+        if (!finite2(rv)) { stop(st, S_NONFINITE); break; }
+        if (rv[0] == 0.0 && rv[1] == 0.0) { stop(st, S_BREAKDOWN); break; }
+        cdiv(st->rho, rv, st->alpha);
+        break;
+    }
+    case ST_OMEGA: {
+        double ts[2] = {s[0], s[1]};
+        double tt = s[2], ss = s[3];
+        if (!(isfinite(tt) && isfinite(ss) && finite2(ts))) { stop(st, S_NONFINITE); break; }
+        if (tt == 0.0) { stop(st, S_BREAKDOWN); break; }
+        double om[2] = {ts[0] / tt, ts[1] / tt};
+        double ohat = sqrt(ts[0] * ts[0] + ts[1] * ts[1]) / sqrt(tt * ss);
+        if (ohat < st->omega0 && ohat > 0.0) {
+            double f = st->omega0 / ohat;
+            om[0] *= f;
+            om[1] *= f;
+        }
+        st->omega[0] = om[0];
+        st->omega[1] = om[1];
+        double c = st->lambda_p / st->gamma_p;
+        st->cXr[0] = c * om[0];
+        st->cXr[1] = c * om[1];
+        st->cXp[0] = c * st->alpha[0];
+        st->cXp[1] = c * st->alpha[1];
+        break;
+    }
+    case ST_RNORM: {
+        double r2 = s[0], x2 = s[1];
+        double rs[2] = {s[2], s[3]};
+        st->g = sqrt(r2);
+        if (st->rescale_x) st->lam = st->sigma_lambda / sqrt(x2);
+        if (st->scale_pass) {
+            st->gam_tmp = st->sigma > 0.0 ? st->sigma / st->g : 1.0;
+            if (!isfinite(st->gam_tmp) || (st->rescale_x && !isfinite(st->lam))) stop(st, S_NONFINITE);
+        } else {
+            end_iteration(st, 1.0, r2, rs);
+        }
+        break;
+    }
+    case ST_END: {
+        double rn2 = s[0];
+        double rs[2] = {s[1], s[2]};
+        double gamma = st->sigma > 0.0 ? (st->recalc ? sqrt(rn2) / st->g : st->gam_tmp) : 1.0;
+        end_iteration(st, gamma, rn2, rs);
+        break;
+    }
+    case ST_OUTER:
+        st->rnorm = sqrt(s[0]);
+        break;
+    case ST_ACC:
+        st->acc += s[0];
+        break;
+    case ST_ACC_SET:
+        st->acc = s[0];
+        break;
+    default:
+        break;
+    }
+}
+
+// ----------------------------------------------------------- reductions ---
+
+// Context of a reducing kernel: each block writes its partial sums; the
+// last block to finish (ticket) adds them in block order (deterministic),
+// runs the scalar stage and re-arms the ticket.
+struct RedCtx {
+    double* partials;    // [gridDim.x][NSUM]
+    unsigned* ticket;    // zero between kernels
+    SolverState* st;
+    int stage;
+};
+
+template <int NSUM>
+__device__ __forceinline__ void warp_sum(double (&v)[NSUM]) {
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
+}
+
+// Sum v over the block; the result is valid in thread 0.
+template <int NSUM>
+__device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
+    __shared__ double sh[NSUM][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_sum<NSUM>(v);
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) sh[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) v[k] = lane < nw ? sh[k][lane] : 0.0;
+        warp_sum<NSUM>(v);
+    }
+}
+
+template <int NSUM>
+__device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc) {
+    __shared__ unsigned is_last;
+    block_sum<NSUM>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) rc.partials[(size_t)blockIdx.x * NSUM + k] = v[k];
+        __threadfence();
+        is_last = (atomicAdd(rc.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) acc[k] += __ldcg(rc.partials + (size_t)b * NSUM + k);
+    }
+    block_sum<NSUM>(acc);
+    if (threadIdx.x == 0) {
+        if (rc.st) run_stage(rc.stage, acc, rc.st);
+        *rc.ticket = 0u;
+        __threadfence();
+    }
+}
+
+// Early exit of every kernel of an inner iteration once the solve is done.
+__device__ __forceinline__ bool solve_done(const SolverState* st) { return st != nullptr && *(volatile const int*)&st->done; }
+
+}  // namespace wd

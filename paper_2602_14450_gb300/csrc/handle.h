@@ -1,0 +1,82 @@
+// Internal state behind the opaque wd_handle of the C ABI.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+
+#include "../../include/wd.h"
+#include "kernels.h"
+
+struct GraphKey {
+    int prec, recon, scale_pass, iters;
+    bool operator<(const GraphKey& o) const {
+        if (prec != o.prec) return prec < o.prec;
+        if (recon != o.recon) return recon < o.recon;
+        if (scale_pass != o.scale_pass) return scale_pass < o.scale_pass;
+        return iters < o.iters;
+    }
+};
+
+struct wd_handle {
+    wd::Geom g{};
+    double kappa = 0.0;
+    int device = 0;
+    std::string err;
+
+    double* U64 = nullptr;             // FP64 links, host layout, on the device
+    bool have_gauge = false;
+    double unit_dev = -1.0, det_dev = -1.0;
+    uint4* links[4][2][2] = {};        // [prec][recon 12 -> 0, 18 -> 1][output parity]
+
+    std::map<std::string, void*> ws;   // named device workspaces
+    wd::SolverState* st = nullptr;     // device scalar state of wd_solve
+    wd::SolverState* hst = nullptr;    // pinned host mirror
+    int* hflag = nullptr;              // pinned: done flags of in-flight graph launches
+    double* partials = nullptr;        // reduction partials
+    unsigned* ticket = nullptr;        // reduction ticket
+    cudaStream_t cap = nullptr;        // capture stream
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace wd {
+
+int fail(wd_handle* h, int code, const char* fmt, ...);
+int cuda_fail(wd_handle* h, cudaError_t e, const char* what);
+void* workspace(wd_handle* h, const std::string& name, size_t bytes);
+int ensure_solver_state(wd_handle* h);
+int ensure_links(wd_handle* h, int prec, int recon, const uint4** even, const uint4** odd);
+size_t vec_bytes(const wd_handle* h, int prec);
+RedCtx red_ctx(wd_handle* h, int stage);
+
+}  // namespace wd
+
+#define WD_CUDA(h, call)                                            \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return wd::cuda_fail((h), e_, #call); \
+    } while (0)
+
+namespace wd {
+
+template <typename T> struct Tag { typedef T type; };
+
+// Call f(Tag<storage type>) for a wd_prec value.
+template <typename F>
+cudaError_t by_prec(int prec, F&& f) {
+    switch (prec) {
+    case WD_FP64: return f(Tag<double>());
+    case WD_FP32: return f(Tag<float>());
+    case WD_FP16: return f(Tag<__half>());
+    case WD_BF16: return f(Tag<__nv_bfloat16>());
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+inline bool valid_prec(int p) { return p == WD_FP64 || p == WD_FP32 || p == WD_FP16 || p == WD_BF16; }
+inline bool valid_recon(int r) { return r == 12 || r == 18; }
+
+}  // namespace wd

@@ -1,0 +1,60 @@
+// Host-side launchers of the device kernels, one instantiation per storage
+// type (translation units ops_f64.cu, ops_f32.cu, ops_f16.cu, ops_bf16.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace wd {
+
+enum Epi { EPI_H = 0, EPI_Y = 1, EPI_YZ = 2 };
+enum Red { RED_NONE = 0, RED_RSV = 1, RED_TS = 2, RED_NORM = 3 };
+
+struct HopParams {
+    Geom g;
+    int parity;             // parity of the output sites
+    const uint4* links;     // gathered links of the output parity
+    const uint4* in;        // input spinor on parity 1 - parity
+    uint4* out;             // output spinor on `parity`
+    const uint4* y;         // epilogue operands on `parity`
+    const uint4* z;
+    const uint4* rstar;     // RED_RSV: sum conj(rstar) out
+    double a, b, c;         // out = a * H in + b * y + c * z
+    RedCtx rc;              // reduction target (partials, ticket, state, stage)
+    const SolverState* guard;  // if set, return at once when guard->done (inner-loop kernels)
+};
+
+// Largest number of blocks any reducing kernel uses (partials capacity).
+constexpr int MAX_RED_BLOCKS = 8192;
+constexpr int MAX_RED_SUMS = 4;
+
+// Units of 16 bytes per site of the gathered links of one parity.
+int link_units(int prec, int recon);
+// Units of 16 bytes per site of a spinor.
+int spinor_units(int prec);
+
+template <typename T> struct Ops {
+    static cudaError_t hop(int recon, int epi, int red, const HopParams& P, cudaStream_t s);
+    static cudaError_t pupdate(int n, uint4* p, const uint4* v, const uint4* r, const SolverState* st, cudaStream_t s);
+    static cudaError_t supdate(int n, uint4* r, const uint4* v, const SolverState* st, cudaStream_t s);
+    static cudaError_t xr(bool with_rs, int n, uint4* x, uint4* r, const uint4* p, const uint4* t, const uint4* rstar,
+                          SolverState* st, RedCtx rc, cudaStream_t s);
+    static cudaError_t scale(int n, uint4* r, uint4* x, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s);
+    static cudaError_t rescale_in(int n, const uint4* r64, uint4* r, uint4* rstar, int ftz, SolverState* st, RedCtx rc,
+                                  cudaStream_t s);
+    static cudaError_t correct(int n, uint4* x64, const uint4* xt, const SolverState* st, cudaStream_t s);
+    static cudaError_t norm2(int n, const uint4* v, RedCtx rc, cudaStream_t s);
+    static cudaError_t pack(const Geom& g, int parity, const double* lex, uint4* out, cudaStream_t s);
+    static cudaError_t unpack(const Geom& g, int parity, const uint4* in, double* lex, cudaStream_t s);
+    static cudaError_t build_links(int recon, const Geom& g, int parity, const double* U, uint4* out, cudaStream_t s);
+};
+
+cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* out, cudaStream_t s);
+
+// Block size of every vector kernel; the hop kernels take theirs from
+// hop_block() (set by the tuner, default 128).
+constexpr int VEC_BLOCK = 256;
+int hop_block();
+void set_hop_block(int b);
+int num_sms();
+
+}  // namespace wd

@@ -1,0 +1,173 @@
+"""Thin ctypes binding of libwd.so (argument marshalling only).
+
+Every function forwards to the C entry point of the same name declared in
+``include/wd.h``; torch tensors are passed as raw device or host pointers and
+streams as ``torch.cuda.Stream.cuda_stream``. There is no fallback: if the
+compiled library is missing, loading raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwd.so")
+
+# enums of wd.h
+WD_OK, WD_ERR_INVALID_ARG, WD_ERR_CUDA, WD_ERR_NOT_SU3 = 0, 1, 2, 3
+WD_ERR_NOT_CONVERGED, WD_ERR_BREAKDOWN, WD_ERR_NONFINITE, WD_ERR_TIMEOUT, WD_ERR_NO_GAUGE = 4, 5, 6, 7, 8
+WD_FP64, WD_FP32, WD_FP16, WD_BF16 = 0, 1, 2, 3
+WD_OP_HOP_EO, WD_OP_HOP_OE, WD_OP_EO_A, WD_OP_FULL = 0, 1, 2, 3
+WD_HOST, WD_DEVICE = 0, 1
+WD_FP64_BICGSTAB, WD_MIXED_FP32, WD_MIXED_FP16_PLAIN, WD_MIXED_FP16, WD_MIXED_BF16 = 0, 1, 2, 3, 4
+
+PREC = {"fp64": WD_FP64, "fp32": WD_FP32, "fp16": WD_FP16, "bf16": WD_BF16}
+SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_plain": WD_MIXED_FP16_PLAIN,
+          "mixed_fp16": WD_MIXED_FP16, "mixed_bf16": WD_MIXED_BF16}
+
+# Exported symbols (the declarations of include/wd.h).
+SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_vector_bytes", "wd_pack",
+           "wd_unpack", "wd_apply", "wd_solve_params_default", "wd_solve", "wd_solve_batch", "wd_status_string",
+           "wd_last_error"]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("s", C.c_double), ("sigma", C.c_double), ("sigma_lambda", C.c_double),
+                ("inner_eps", C.c_double), ("omega0", C.c_double), ("recalc_gamma", C.c_int),
+                ("rescale_x", C.c_int), ("use_shat", C.c_int), ("x_is_guess", C.c_int), ("max_outer", C.c_int),
+                ("max_inner", C.c_int), ("recon", C.c_int), ("ftz", C.c_int), ("iters_per_sync", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iterations", C.c_int), ("inner_iterations", C.c_int),
+                ("inner_matvecs", C.c_int), ("outer_matvecs", C.c_int), ("true_residual", C.c_double),
+                ("outer_residual", C.c_double), ("elapsed_ms", C.c_double),
+                ("first_inner_nonzeros", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libwd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_2602_14450_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        L.wd_create.argtypes = [C.POINTER(C.c_int), d, C.POINTER(C.c_int), C.POINTER(vp)]
+        L.wd_destroy.argtypes = [vp]
+        L.wd_set_gauge.argtypes = [vp, vp, i]
+        L.wd_gauge_unitarity.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        L.wd_vector_bytes.argtypes = [vp, i]
+        L.wd_vector_bytes.restype = sz
+        L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
+        L.wd_unpack.argtypes = [vp, i, i, vp, vp, vp]
+        L.wd_apply.argtypes = [vp, i, i, i, vp, vp, vp]
+        L.wd_solve_params_default.argtypes = [i, C.POINTER(SolveParams)]
+        L.wd_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
+        L.wd_solve_batch.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(vp), d, i,
+                                     C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
+        L.wd_status_string.argtypes = [i]
+        L.wd_status_string.restype = C.c_char_p
+        L.wd_last_error.argtypes = [vp]
+        L.wd_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class WDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{lib().wd_status_string(code).decode()}: {msg}")
+        self.code = code
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def default_params(scheme) -> SolveParams:
+    p = SolveParams()
+    rc = lib().wd_solve_params_default(SCHEME.get(scheme, scheme), C.byref(p))
+    if rc:
+        raise WDError(rc, "wd_solve_params_default")
+    return p
+
+
+class Lattice:
+    """One wd_handle: lattice geometry, kappa, boundary phases and gauge field."""
+
+    def __init__(self, dims, kappa, bc=(1, 1, 1, -1)):
+        self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        d = (C.c_int * 4)(*self.dims)
+        b = (C.c_int * 4)(*bc)
+        h = C.c_void_p()
+        rc = lib().wd_create(d, self.kappa, b, C.byref(h))
+        if rc:
+            raise WDError(rc, f"wd_create{self.dims}")
+        self.h = h
+
+    def _check(self, rc, what):
+        if rc not in (WD_OK,):
+            raise WDError(rc, f"{what}: {lib().wd_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().wd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gauge(self, u):
+        """u: float64 tensor in the host layout [4, V, 3, 3, 2] (CPU or CUDA)."""
+        where = WD_DEVICE if u.is_cuda else WD_HOST
+        self._check(lib().wd_set_gauge(self.h, _ptr(u.contiguous()), where), "wd_set_gauge")
+
+    def unitarity(self):
+        a, b = C.c_double(), C.c_double()
+        self._check(lib().wd_gauge_unitarity(self.h, C.byref(a), C.byref(b)), "wd_gauge_unitarity")
+        return a.value, b.value
+
+    def vector_bytes(self, prec):
+        return int(lib().wd_vector_bytes(self.h, PREC.get(prec, prec)))
+
+    def pack(self, prec, parity, lex, packed, stream=None):
+        self._check(lib().wd_pack(self.h, PREC.get(prec, prec), parity, _ptr(lex), _ptr(packed), _stream(stream)),
+                    "wd_pack")
+
+    def unpack(self, prec, parity, packed, lex, stream=None):
+        self._check(lib().wd_unpack(self.h, PREC.get(prec, prec), parity, _ptr(packed), _ptr(lex), _stream(stream)),
+                    "wd_unpack")
+
+    def apply(self, prec, recon, op, x, y, stream=None):
+        self._check(lib().wd_apply(self.h, PREC.get(prec, prec), recon, op, _ptr(x), _ptr(y), _stream(stream)),
+                    "wd_apply")
+
+    def solve(self, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):
+        """Solve D_W x = b; b, x float64 full-lattice tensors (host layout), CPU or CUDA."""
+        sc = SCHEME.get(scheme, scheme)
+        prm = params if params is not None else default_params(sc)
+        st = SolveStats()
+        rc = lib().wd_solve(self.h, _ptr(b), _ptr(x), float(tol), sc, C.byref(prm), C.byref(st), _stream(stream))
+        if check:
+            self._check(rc, "wd_solve")
+        return st

@@ -1,0 +1,98 @@
+"""Parity of the CUDA hopping kernels (wd_apply) with the float64 oracle (Eq. 1, Eq. 4)."""
+
+import pytest
+import torch
+
+from oracle import wilson as W
+from paper_2602_14450_gb300 import synth, wd
+from tests.gpu_util import TOL, apply_op, gauge_host, lattice, rel_l2
+
+pytestmark = pytest.mark.gpu
+BC = (1, 1, 1, -1)
+
+# extents: the smallest lattice (neighbours coincide), one block, several
+# blocks with a ragged tail (V/2 = 384, 960), mixed extents
+DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 4, 8), (8, 6, 4, 10)]
+
+
+def oracle_op(u, psi, op, kappa):
+    if op == wd.WD_OP_HOP_EO:
+        return W.hop_pq(u, psi, 0, BC)
+    if op == wd.WD_OP_HOP_OE:
+        return W.hop_pq(u, psi, 1, BC)
+    if op == wd.WD_OP_EO_A:
+        return W.eo_operator(u, W.restrict(psi, 0), kappa, BC)
+    return W.dirac(u, psi, kappa, BC)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_operators_match_oracle(dims, prec, recon):
+    u = synth.gauge_random(dims, 0.5, seed=7)
+    psi = synth.gaussian_source(dims, seed=8)
+    kappa = 0.127
+    lat = lattice(u, kappa, dims)
+    for op in (wd.WD_OP_HOP_EO, wd.WD_OP_HOP_OE, wd.WD_OP_EO_A, wd.WD_OP_FULL):
+        got = apply_op(lat, prec, recon, op, psi, dims)
+        want = oracle_op(u, psi, op, kappa)
+        err = rel_l2(got, want)
+        assert err <= TOL[prec], (op, err)
+        if prec == "fp64":
+            assert torch.allclose(got, want, rtol=0, atol=1e-13 * want.abs().max().item())
+
+
+def test_boundary_phases_follow_bc():
+    dims = (4, 4, 4, 6)
+    u = synth.gauge_random(dims, 0.5, seed=1)
+    psi = synth.gaussian_source(dims, seed=2)
+    for bc in [(1, 1, 1, 1), (-1, 1, -1, -1), (1, -1, 1, 1)]:
+        lat = wd.Lattice(dims, 0.1, bc)
+        lat.set_gauge(gauge_host(u))
+        got = apply_op(lat, "fp64", 18, wd.WD_OP_FULL, psi, dims)
+        assert rel_l2(got, W.dirac(u, psi, 0.1, bc)) < 1e-14
+
+
+def test_twelve_real_links_refused_for_non_su3():
+    dims = (4, 4, 4, 4)
+    u = 1.01 * synth.gauge_random(dims, 0.5, seed=3)
+    lat = lattice(u, 0.12, dims)
+    dev, ddet = lat.unitarity()
+    assert dev > 1e-3 and ddet > 1e-3
+    psi = synth.gaussian_source(dims, seed=4)
+    with pytest.raises(wd.WDError) as e:
+        apply_op(lat, "fp16", 12, wd.WD_OP_HOP_EO, psi, dims)
+    assert e.value.code == wd.WD_ERR_NOT_SU3
+    # 18-real storage has no such requirement
+    got = apply_op(lat, "fp64", 18, wd.WD_OP_HOP_EO, psi, dims)
+    assert rel_l2(got, W.hop_pq(u, psi, 0, BC)) < 1e-13
+
+
+def test_apply_before_gauge_is_an_error():
+    lat = wd.Lattice((4, 4, 4, 4), 0.12)
+    x = torch.zeros(lat.vector_bytes("fp16"), dtype=torch.uint8, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(wd.WDError) as e:
+        lat.apply("fp16", 12, wd.WD_OP_HOP_EO, x, y)
+    assert e.value.code == wd.WD_ERR_NO_GAUGE
+
+
+@pytest.mark.parametrize("prec,recon", [("fp16", 12), ("fp64", 18)])
+def test_full_size_sampled_sites(prec, recon):
+    # 32^3 x 64 in the launch configuration of the benchmark; the oracle
+    # evaluates Eq. 1 at sampled sites (all boundary corners included).
+    dims = (32, 32, 32, 64)
+    u = synth.gauge_random(dims, 0.5, seed=20260214)
+    psi = synth.gaussian_source(dims, seed=450)
+    lat = lattice(u, 0.13, dims)
+    got = apply_op(lat, prec, recon, wd.WD_OP_HOP_EO, psi, dims).reshape(-1, 4, 3)
+    par = W.parity(dims).reshape(-1)
+    g = torch.Generator().manual_seed(0)
+    even = torch.nonzero(par == 0).reshape(-1)
+    sample = even[torch.randint(len(even), (4000,), generator=g)]
+    corners = torch.tensor([0, 31, 32 * 31, 32 ** 3 * 63, 32 ** 3 * 64 - 1, 32 ** 3 * 64 - 32])
+    sites = torch.cat([sample, corners[par[corners] == 0]])
+    want = W.hop_at_sites(u, psi, sites, BC)
+    assert rel_l2(got[sites], want) <= TOL[prec]
+    odd = torch.nonzero(par == 1).reshape(-1)[:1000]
+    assert torch.count_nonzero(got[odd]) == 0

@@ -1,0 +1,177 @@
+"""wd_solve against the oracle: final FP64 residual, solution, iteration counts, faults."""
+
+import math
+
+import pytest
+import torch
+
+from oracle import solvers as S
+from oracle import wilson as W
+from paper_2602_14450_gb300 import synth, wd
+from tests.gpu_util import from_lex, lattice, lex_dev
+
+pytestmark = pytest.mark.gpu
+BC = (1, 1, 1, -1)
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    # 8^4, exp(i eps H) links (eps = 0.5), kappa = 0.12, Gaussian source
+    dims = (8, 8, 8, 8)
+    u = synth.gauge_random(dims, 0.5, seed=20260214)
+    eta = synth.gaussian_source(dims, seed=450)
+    ref, info = S.solve_wilson(u, eta, 0.12, BC, tol=1e-13)
+    return dims, u, eta, 0.12, ref
+
+
+@pytest.fixture(scope="module")
+def smeared():
+    dims = (8, 8, 8, 8)
+    u = synth.gauge_smeared(dims, seed=20260214)
+    eta = synth.gaussian_source(dims, seed=450)
+    return dims, u, eta, 0.13
+
+
+def check_solution(dims, u, eta, kappa, x, ref=None):
+    res = S.norm(eta - W.dirac(u, x, kappa, BC)) / S.norm(eta)
+    assert res <= TOL, res
+    if ref is not None:
+        assert S.norm(x - ref) / S.norm(ref) < 1e-8
+
+
+SCHEMES = ["fp64", "mixed_fp32", "mixed_fp16_plain", "mixed_fp16", "mixed_bf16"]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_schemes_reach_fp64_residual(cfg0, scheme):
+    dims, u, eta, kappa, ref = cfg0
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, scheme)
+    assert st.status == wd.WD_OK
+    assert st.true_residual <= TOL
+    check_solution(dims, u, eta, kappa, from_lex(x, dims), ref)
+
+
+def test_alg4_solution_rescaling(cfg0):
+    dims, u, eta, kappa, ref = cfg0
+    lat = lattice(u, kappa, dims)
+    p = wd.default_params("mixed_fp16")
+    p.sigma, p.sigma_lambda, p.rescale_x = 256.0, 256.0, 1
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "mixed_fp16", params=p)
+    assert st.status == wd.WD_OK
+    check_solution(dims, u, eta, kappa, from_lex(x, dims), ref)
+
+
+@pytest.mark.parametrize("recon", [12, 18])
+def test_host_buffers_match_device_buffers(cfg0, recon):
+    dims, u, eta, kappa, _ = cfg0
+    lat = lattice(u, kappa, dims)
+    p = wd.default_params("mixed_fp16")
+    p.recon = recon
+    bh = synth.to_host_layout(eta)
+    xh = torch.zeros_like(bh)
+    st_h = lat.solve(bh, xh, TOL, "mixed_fp16", params=p)
+    xd = torch.zeros_like(bh).cuda()
+    st_d = lat.solve(bh.cuda(), xd, TOL, "mixed_fp16", params=p)
+    assert st_h.status == st_d.status == wd.WD_OK
+    assert torch.equal(xh, xd.cpu())
+    assert st_h.inner_matvecs == st_d.inner_matvecs
+
+
+def test_restart_from_solution(cfg0):
+    dims, u, eta, kappa, _ = cfg0
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    lat.solve(b, x, TOL, "mixed_fp16")
+    p = wd.default_params("mixed_fp16")
+    p.x_is_guess = 1
+    st = lat.solve(b, x, TOL, "mixed_fp16", params=p)
+    assert st.status == wd.WD_OK and st.outer_iterations == 0 and st.inner_matvecs == 0
+
+
+def test_matvec_counts_match_emulated_oracle(smeared):
+    # The oracle runs Alg. 2 + Alg. 3 with FP16 storage emulated on the same
+    # inputs; counts agree within 15% (arithmetic and summation order differ).
+    dims, u, eta, kappa = smeared
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    for scheme, fmt, outer, inner in [
+        ("mixed_fp16", "fp16", S.OuterParams(s=128.0), S.InnerParams(sigma=64.0)),
+        ("mixed_fp16_plain", "fp16", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None)),
+        ("mixed_fp32", "fp32", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None)),
+    ]:
+        x = torch.zeros_like(b)
+        p = wd.default_params(scheme)
+        p.recon = 18
+        st = lat.solve(b, x, TOL, scheme, params=p)
+        assert st.status == wd.WD_OK
+        _, tr = S.solve_wilson_mixed(u, eta, kappa, BC, fmt=fmt, outer=outer, inner=inner)
+        assert abs(st.inner_matvecs - tr.matvecs) <= 0.15 * tr.matvecs + 4, (scheme, st.inner_matvecs, tr.matvecs)
+    # FP64 BiCGStab (Alg. 3 with gamma = 1) against the oracle's float64 run of the same recurrence
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "fp64")
+    bhat = W.eo_source(u, eta, kappa, BC)
+    a = lambda f: W.eo_operator(u, f, kappa, BC)
+    prm = S.InnerParams(sigma=None, eps=0.5 * TOL * S.norm(eta) / S.norm(bhat), max_matvecs=100000)
+    _, tr = S.bicgstab_rescaled(a, bhat, prm)
+    assert abs(st.inner_matvecs - tr.matvecs) <= 0.05 * tr.matvecs + 2
+
+
+def test_first_inner_input_single_nonzero():
+    # Sec. 5: b = (1, 0, ..., 0) on the even-odd system: one nonzero real in
+    # the first low-precision input.
+    dims = (8, 8, 8, 8)
+    u = synth.gauge_smeared(dims, seed=1)
+    lat = lattice(u, 0.13, dims)
+    eta = synth.point_source(dims, 0, 0, site=0)
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, 1e-8, "mixed_fp16")
+    assert st.first_inner_nonzeros == 1
+
+
+def test_nan_source_reports_nonfinite(cfg0):
+    dims, u, eta, kappa, _ = cfg0
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    b[0, 0, 0, 3, 1, 2, 0] = math.nan
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "mixed_fp16", check=False)
+    assert st.status == wd.WD_ERR_NONFINITE
+    # the handle stays usable
+    b = lex_dev(eta)
+    st = lat.solve(b, x, TOL, "mixed_fp16")
+    assert st.status == wd.WD_OK
+
+
+def test_iteration_caps_report_not_converged(cfg0):
+    dims, u, eta, kappa, _ = cfg0
+    lat = lattice(u, kappa, dims)
+    p = wd.default_params("mixed_fp16")
+    p.max_outer = 1
+    p.max_inner = 4
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "mixed_fp16", params=p, check=False)
+    assert st.status == wd.WD_ERR_NOT_CONVERGED
+    assert st.outer_iterations == 1 and st.inner_matvecs <= 4 + 2
+    assert torch.isfinite(x).all()
+
+
+@pytest.mark.parametrize("scale", [1e-150, 1e150])
+def test_extreme_source_norms(cfg0, scale):
+    # The outer rescaling (Alg. 2) keeps the FP16 inner input at norm s for
+    # any |b|; a first rho' = |r|^2 keeps beta = 1 (Sec. 3).
+    dims, u, eta, kappa, ref = cfg0
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta) * scale
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "mixed_fp16")
+    assert st.status == wd.WD_OK
+    assert S.norm(from_lex(x, dims) / scale - ref) / S.norm(ref) < 1e-8
