@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark: time to |b - D x| / |b| <= 1e-10 for the Wilson-Dirac system on
+32^3 x 64 with the mixed FP16/FP64 solver (Alg. 2 + Alg. 3), beside the pure
+FP64 and FP32-mixed forms, and the FP16 Dslash against the HBM roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full solve (even-odd source, refinement with FP16 inner
+BiCGStab, odd reconstruction, FP64 true residual) of a synthetic workload
+whose inputs (402 MB FP64 source, 402 MB FP16 links, 1.2 GB FP64 links) are
+all larger than the 129 MB L2. Rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to ‖r‖/‖b‖≤1e-10 at 32^3×64, FP16-mixed vs FP64; Dslash GB/s vs HBM peak"
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32x32x32x64")
+    ap.add_argument("--dslash-launches", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and FP32-mixed solves")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.uuid], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_iteration_seconds(u_cpu, eta, kappa, iters):
+    """Seconds per float64 BiCGStab iteration of the oracle on the even-odd system."""
+    import torch
+
+    from oracle import solvers as S
+    from oracle import wilson as W
+    b = W.eo_source(u_cpu, eta, kappa)
+    a = lambda f: W.eo_operator(u_cpu, f, kappa)
+    t0 = time.perf_counter()
+    S.bicgstab(a, b, 0.0, maxiter=iters)
+    return (time.perf_counter() - t0) / iters, torch.get_num_threads()
+
+
+def stored_oracle_iterations(dims):
+    """Float64 BiCGStab iterations the oracle needs on this workload, if recorded."""
+    name = "x".join(str(d) for d in dims)
+    path = os.path.join(ROOT, "tests", "golden", f"fp64_iterations_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("iterations"):
+                return int(line.split()[1])
+    return None
+
+
+def reference_arm(args, rank, ws):
+    """The oracle on the host cores (the reference of this workload); rank 0 only."""
+    if rank != 0:
+        return
+    import torch
+
+    from paper_2602_14450_gb300 import workloads
+    wl = workloads.get(args.workload)
+    n_iter = stored_oracle_iterations(wl.dims)
+    if n_iter is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's float64 iteration count for this "
+                          "workload has not been recorded (tests/golden)"}))
+        return
+    u = wl.gauge(device="cpu")
+    eta = wl.source()
+    for _ in range(args.warmup):
+        oracle_iteration_seconds(u, eta, wl.kappa, 1)
+    per = []
+    for _ in range(args.steps):
+        s, cores = oracle_iteration_seconds(u, eta, wl.kappa, 1)
+        per.append(s)
+    value = statistics.median(per) * n_iter
+    sample = (f"{args.steps} single float64 BiCGStab iterations of the oracle (explicit-gamma D_W, even-odd) on the "
+              f"{args.workload} workload, median scaled by the {n_iter} iterations the oracle needs to 1e-10")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(per) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"wilson_eo_{args.workload}", "kappa": wl.kappa, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def dslash_bandwidth(lat, wd, prec, recon, vh, launches, torch):
+    """Average duration of the hop kernel (H_eo, output on even sites) and its algorithmic GB/s."""
+    nb = lat.vector_bytes(prec)
+    ins = [torch.randint(0, 1 << 14, (nb // 2,), dtype=torch.int16, device="cuda") for _ in range(4)]
+    if prec in ("fp32", "fp64"):
+        ins = [torch.randn(nb // 8, dtype=torch.float64, device="cuda") for _ in range(4)]
+    out = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for i in range(5):
+        lat.apply(prec, recon, wd.WD_OP_HOP_EO, ins[i % 4], out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(launches):
+        lat.apply(prec, recon, wd.WD_OP_HOP_EO, ins[i % 4], out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / launches
+    ebytes = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec]
+    per_site = 2 * 24 * ebytes + 8 * recon * ebytes
+    return {"us": us, "bytes_per_site": per_site, "gbs": per_site * vh / (us * 1e-6) / 1e9}
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, rank, ws)
+    import torch
+
+    import __graft_entry__
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_2602_14450_gb300 import synth, wd, workloads
+
+    wl = workloads.get(args.workload)
+    vh = wl.volume // 2
+    u = wl.gauge(device="cuda")
+    eta = wl.source()
+    lat = wd.Lattice(wl.dims, wl.kappa)
+    lat.set_gauge(torch.view_as_real(u).contiguous())
+    b = synth.to_host_layout(eta).cuda()
+    x = torch.zeros_like(b)
+    prm = wd.default_params("mixed_fp16")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        st = lat.solve(b, x, TOL, "mixed_fp16", prm, stream)
+    props = torch.cuda.get_device_properties(local)
+    clocks = Clocks(f"GPU-{props.uuid}" if not str(props.uuid).startswith("GPU-") else str(props.uuid))
+
+    # timed region: K full solves on device-resident inputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(lat.solve(b, x, TOL, "mixed_fp16", prm, stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+    st = stats[-1]
+    launches = sum(s.kernel_launches for s in stats)
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    lat.solve(bh, xh, TOL, "mixed_fp16", prm, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat.solve(bh, xh, TOL, "mixed_fp16", prm, stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
+
+    forms = {"mixed_fp16": {"time_s": ms / 1e3, "inner_matvecs": st.inner_matvecs,
+                            "outer_iterations": st.outer_iterations, "true_residual": st.true_residual}}
+    if not args.no_forms:
+        for scheme in ("mixed_fp32", "fp64"):
+            p = wd.default_params(scheme)
+            xs = torch.zeros_like(b)
+            q = wd.default_params(scheme)
+            q.max_inner, q.max_outer = 4, 1
+            lat.solve(b, xs, TOL, scheme, q, stream, check=False)   # links, workspaces and graph
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            s2 = lat.solve(b, xs, TOL, scheme, p, stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            forms[scheme] = {"time_s": f0.elapsed_time(f1) / 1e3, "inner_matvecs": s2.inner_matvecs,
+                             "outer_iterations": s2.outer_iterations, "true_residual": s2.true_residual}
+
+    # Dslash: the dominant kernel of the inner solve, timed alone on the launching stream
+    sweep = {}
+    for prec, recon in (("fp16", 12), ("fp16", 18), ("fp32", 12), ("fp32", 18), ("fp64", 18)):
+        sweep[f"{prec}_{recon}"] = dslash_bandwidth(lat, wd, prec, recon, vh, args.dslash_launches, torch)
+    peak, peak_kind = measured_peaks()
+    top = sweep["fp16_12"]
+    roof = {"bound": "hbm", "achieved": top["gbs"], "peak": peak, "unit": "GB/s", "frac": top["gbs"] / peak,
+            "traffic": None, "kernel": "hop_kernel<__half,12,EPI_H,RED_NONE> (H_eo, FP16, 12-real links)",
+            "peak_kind": peak_kind, "bytes_per_site": top["bytes_per_site"], "sites_per_launch": vh,
+            "avg_launch_us": top["us"]}
+
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 storage / f32 arithmetic / f64 refinement", "data": "synthetic",
+        "config": {"workload": f"wilson_eo_{args.workload}", "lattice": list(wl.dims), "kappa": wl.kappa,
+                   "links": "exp(i 0.5 H) + 3 APE steps (alpha 0.5), SU(3)-reprojected; FP16 12-real in the inner solve",
+                   "source": f"Gaussian, seed {wl.source_seed}", "tol": TOL,
+                   "scheme": "Alg. 2 + Alg. 3 (s=128, sigma=64, recalculated gamma, eps^2=1e-4)",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": bh.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "forms": forms,
+        "speedup_vs_fp64": (forms["fp64"]["time_s"] / forms["mixed_fp16"]["time_s"]) if "fp64" in forms else None,
+        "dslash_sweep": sweep,
+        "solve": st.as_dict(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n_iter = stored_oracle_iterations(wl.dims)
+        ref = "oracle"
+        if n_iter is None and "fp64" in forms:
+            n_iter = forms["fp64"]["inner_matvecs"] // 2
+            ref = "GPU float64 solve of the same recurrence"
+        if n_iter:
+            s_it, cores = oracle_iteration_seconds(u.cpu(), eta, wl.kappa, 2)
+            line["cpu_baseline"] = {
+                "value": s_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle",
+                "sample": f"2 float64 BiCGStab iterations of the oracle on the full {args.workload} workload "
+                          f"({s_it:.2f} s each), scaled by the {n_iter} iterations to 1e-10 ({ref} count)"}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

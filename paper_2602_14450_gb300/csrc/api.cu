@@ -1,6 +1,7 @@
 // C ABI entry points: handle lifetime, gauge upload and link packing, vector
 // packing, and operator application (wd.h).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -11,6 +12,15 @@ namespace wd {
 static int g_hop_block = 128;
 int hop_block() { return g_hop_block; }
 void set_hop_block(int b) { g_hop_block = b; }
+
+int hop_variant() {
+    static int v = 0;
+    if (v == 0) {
+        const char* e = std::getenv("WD_HOP_KERNEL");
+        v = (e && e[0] == '2') ? 2 : 1;
+    }
+    return v;
+}
 
 int num_sms() {
     static int n = 0;

@@ -55,6 +55,10 @@ cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* ou
 constexpr int VEC_BLOCK = 256;
 int hop_block();
 void set_hop_block(int b);
+// Hop kernel for FP32-arithmetic storage types: 1 = one site per thread
+// (default), 2 = two sites per thread with packed FP32x2 math. Read once from
+// the environment variable WD_HOP_KERNEL.
+int hop_variant();
 int num_sms();
 
 }  // namespace wd

@@ -3,9 +3,11 @@
 
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include "blas_impl.cuh"
+#include "hop2_impl.cuh"
 #include "hop_impl.cuh"
 #include "kernels.h"
 
@@ -43,6 +45,15 @@ inline int stream_grid(int n, int block) {
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     const int block = hop_block();
+    if constexpr (!std::is_same<T, double>::value) {
+        if (hop_variant() == 2) {   // two sites per thread, packed FP32x2 arithmetic
+            const int n = P.g.Vh / 2;
+            const void* k2 = (const void*)hop2_kernel<T, R, E, D>;
+            const int grid = (D == RED_NONE) ? stream_grid(n, block) : reduce_grid(k2, n, block);
+            hop2_kernel<T, R, E, D><<<grid, block, 0, s>>>(P);
+            return cudaGetLastError();
+        }
+    }
     const void* k = (const void*)hop_kernel<T, R, E, D>;
     const int grid = (D == RED_NONE) ? stream_grid(P.g.Vh, block) : reduce_grid(k, P.g.Vh, block);
     hop_kernel<T, R, E, D><<<grid, block, 0, s>>>(P);

@@ -18,8 +18,10 @@ Conventions (shared by every consumer):
 
 Random numbers come from numpy's PCG64 so that a seed gives the same draws on
 x86-64 and aarch64. Floating-point post-processing (exp, smearing) runs in
-float64 torch CPU ops; results may differ between machines in the last bits,
-so consumers always generate once and hand the same tensor to both sides.
+float64 torch ops on the CPU, or on a CUDA device when ``device`` says so (a
+large lattice is generated in seconds there); results may differ between
+machines and devices in the last bits, so consumers generate once and hand
+the same tensor to both sides.
 """
 
 from __future__ import annotations
@@ -62,28 +64,42 @@ def _dagger(m: torch.Tensor) -> torch.Tensor:
 
 
 def _expi_hermitian(h: torch.Tensor, eps: float) -> torch.Tensor:
-    """exp(i*eps*h) for a batch of Hermitian matrices, by eigendecomposition."""
-    e, q = torch.linalg.eigh(h)
-    ph = torch.exp(1j * eps * e.to(CDT))
-    return (q * ph.unsqueeze(-2)) @ _dagger(q)
+    """exp(i*eps*h) for a batch of Hermitian matrices (Pade scaling and squaring)."""
+    return torch.linalg.matrix_exp((1j * eps) * h)
 
 
-def random_su3(n: int, eps: float, rng: np.random.Generator, chunk: int = 1 << 20) -> torch.Tensor:
+def _inverse_and_det(w: torch.Tensor):
+    """Inverse and determinant of a batch of 3x3 matrices via the adjugate."""
+    n = w.shape[0]
+    a = w.reshape(n, 9).T.contiguous()          # a[3 i + j] = w[:, i, j]
+    cof = [None] * 9
+    for i in range(3):
+        r0, r1 = [k for k in range(3) if k != i]
+        for j in range(3):
+            c0, c1 = [k for k in range(3) if k != j]
+            minor = a[3 * r0 + c0] * a[3 * r1 + c1] - a[3 * r0 + c1] * a[3 * r1 + c0]
+            cof[3 * i + j] = minor if (i + j) % 2 == 0 else -minor
+    det = a[0] * cof[0] + a[1] * cof[1] + a[2] * cof[2]
+    inv = torch.stack([cof[3 * j + i] for i in range(3) for j in range(3)]) / det
+    return inv.T.reshape(n, 3, 3), det
+
+
+def random_su3(n: int, eps: float, rng: np.random.Generator, chunk: int = 1 << 20, device="cpu") -> torch.Tensor:
     """n matrices exp(i*eps*H), H = sum_a h_a lambda_a / 2 with h_a ~ N(0, 1).
 
     The draws are taken as one [n, 8] block (row = matrix), so the result does
     not depend on ``chunk``.
     """
     h = torch.from_numpy(rng.standard_normal((n, 8)))
-    lam = gell_mann() / 2
-    out = torch.empty((n, 3, 3), dtype=CDT)
+    lam = (gell_mann() / 2).to(device)
+    out = torch.empty((n, 3, 3), dtype=CDT, device=device)
     for s in range(0, n, chunk):
-        hs = torch.einsum("na,aij->nij", h[s:s + chunk].to(CDT), lam)
+        hs = torch.einsum("na,aij->nij", h[s:s + chunk].to(device=device, dtype=CDT), lam)
         out[s:s + chunk] = _expi_hermitian(hs, eps)
     return out
 
 
-def gauge_random(dims, eps: float = 0.5, seed: int = 0) -> torch.Tensor:
+def gauge_random(dims, eps: float = 0.5, seed: int = 0, device="cpu") -> torch.Tensor:
     """Links U_mu(x) = exp(i*eps*H) with independent Gaussian traceless Hermitian H.
 
     Draw order: the [4*V, 8] block of N(0,1) numbers is indexed (mu, site, a).
@@ -91,7 +107,7 @@ def gauge_random(dims, eps: float = 0.5, seed: int = 0) -> torch.Tensor:
     lx, ly, lz, lt = _check_dims(dims)
     n = 4 * lx * ly * lz * lt
     rng = np.random.Generator(np.random.PCG64(seed))
-    return random_su3(n, eps, rng).reshape(4, lt, lz, ly, lx, 3, 3)
+    return random_su3(n, eps, rng, device=device).reshape(4, lt, lz, ly, lx, 3, 3)
 
 
 def _shift(f: torch.Tensor, mu: int, step: int) -> torch.Tensor:
@@ -110,15 +126,16 @@ def su3_project(v: torch.Tensor, iters: int = 30, tol: float = 1e-15) -> torch.T
     """
     shape = v.shape
     w = v.reshape(-1, 3, 3).clone()
-    eye = torch.eye(3, dtype=CDT)
-    for _ in range(iters):
-        zeta = torch.linalg.det(w).abs().pow(-1.0 / 3.0).to(CDT)[:, None, None]
-        ws = zeta * w
-        w = 0.5 * (ws + _dagger(torch.linalg.inv(ws)))
-        dev = (_dagger(w) @ w - eye).abs().amax().item()
-        if dev < tol:
-            break
-    d = torch.linalg.det(w)
+    eye = torch.eye(3, dtype=CDT, device=v.device)
+    for it in range(iters):
+        inv, det = _inverse_and_det(w)
+        zeta = det.abs().pow(-1.0 / 3.0).to(CDT)[:, None, None]
+        w = 0.5 * (zeta * w + _dagger(inv) / zeta)
+        if it >= 4:
+            dev = (_dagger(w) @ w - eye).abs().amax().item()
+            if dev < tol:
+                break
+    _, d = _inverse_and_det(w)
     w = w * torch.exp(-1j * torch.angle(d) / 3.0)[:, None, None]
     return w.reshape(shape)
 
@@ -145,9 +162,9 @@ def ape_smear(u: torch.Tensor, alpha: float = 0.5, steps: int = 3) -> torch.Tens
     return u
 
 
-def gauge_smeared(dims, seed: int, eps: float = 0.5, alpha: float = 0.5, steps: int = 3) -> torch.Tensor:
+def gauge_smeared(dims, seed: int, eps: float = 0.5, alpha: float = 0.5, steps: int = 3, device="cpu") -> torch.Tensor:
     """Random exp(i*eps*H) links followed by ``steps`` APE steps with SU(3) reprojection."""
-    return ape_smear(gauge_random(dims, eps, seed), alpha, steps)
+    return ape_smear(gauge_random(dims, eps, seed, device=device), alpha, steps)
 
 
 def gauge_unit(dims) -> torch.Tensor:
