@@ -55,12 +55,21 @@ int cuda_fail(wd_handle* h, cudaError_t e, const char* what) {
 size_t vec_bytes(const wd_handle* h, int prec) { return (size_t)h->g.Vh * spinor_units(prec) * 16; }
 
 void* workspace(wd_handle* h, const std::string& name, size_t bytes) {
-    auto it = h->ws.find(name);
-    if (it != h->ws.end()) return it->second;
-    void* p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-    h->ws[name] = p;
-    return p;
+    Buffer& b = h->ws[name];
+    if (b.p && b.bytes >= bytes) return b.p;
+    if (b.p) {
+        cudaDeviceSynchronize();
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        b.p = nullptr;
+        return nullptr;
+    }
+    b.bytes = bytes;
+    ++h->gen;
+    return b.p;
 }
 
 RedCtx red_ctx(wd_handle* h, int stage) {
@@ -72,19 +81,35 @@ RedCtx red_ctx(wd_handle* h, int stage) {
     return rc;
 }
 
-int ensure_solver_state(wd_handle* h) {
-    if (h->st) return WD_OK;
-    WD_CUDA(h, cudaMalloc(&h->st, sizeof(SolverState)));
-    WD_CUDA(h, cudaMemset(h->st, 0, sizeof(SolverState)));
-    WD_CUDA(h, cudaMalloc(&h->partials, sizeof(double) * MAX_RED_BLOCKS * MAX_RED_SUMS));
-    WD_CUDA(h, cudaMalloc(&h->ticket, sizeof(unsigned)));
-    WD_CUDA(h, cudaMemset(h->ticket, 0, sizeof(unsigned)));
-    WD_CUDA(h, cudaMallocHost(&h->hst, sizeof(SolverState)));
-    WD_CUDA(h, cudaMallocHost(&h->hflag, 2 * sizeof(int)));
-    WD_CUDA(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; ++i) WD_CUDA(h, cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming));
-    WD_CUDA(h, cudaEventCreate(&h->t0));
-    WD_CUDA(h, cudaEventCreate(&h->t1));
+int ensure_solver_state(wd_handle* h, int nrhs) {
+    if (!h->cap) {
+        WD_CUDA(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) WD_CUDA(h, cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming));
+        WD_CUDA(h, cudaEventCreate(&h->t0));
+        WD_CUDA(h, cudaEventCreate(&h->t1));
+        WD_CUDA(h, cudaMalloc(&h->dflag, sizeof(int)));
+        WD_CUDA(h, cudaMallocHost(&h->hflag, 2 * sizeof(int)));
+    }
+    if (h->cap_rhs >= nrhs) return WD_OK;
+    WD_CUDA(h, cudaDeviceSynchronize());
+    if (h->st) cudaFree(h->st);
+    if (h->partials) cudaFree(h->partials);
+    if (h->ticket) cudaFree(h->ticket);
+    if (h->hst) cudaFreeHost(h->hst);
+    h->st = nullptr;
+    h->partials = nullptr;
+    h->ticket = nullptr;
+    h->hst = nullptr;
+    h->cap_rhs = 0;
+    WD_CUDA(h, cudaMalloc(&h->st, sizeof(SolverState) * nrhs));
+    WD_CUDA(h, cudaMemset(h->st, 0, sizeof(SolverState) * nrhs));
+    WD_CUDA(h, cudaMalloc(&h->partials, sizeof(double) * RED_STRIDE * nrhs));
+    WD_CUDA(h, cudaMalloc(&h->ticket, sizeof(unsigned) * nrhs));
+    WD_CUDA(h, cudaMemset(h->ticket, 0, sizeof(unsigned) * nrhs));
+    WD_CUDA(h, cudaMallocHost(&h->hst, sizeof(SolverState) * nrhs));
+    std::memset(h->hst, 0, sizeof(SolverState) * nrhs);
+    h->cap_rhs = nrhs;
+    ++h->gen;
     return WD_OK;
 }
 
@@ -206,7 +231,9 @@ int wd_destroy(wd_handle* h) {
     if (!h) return WD_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    for (auto& kv : h->ws) cudaFree(kv.second);
+    for (auto& kv : h->ws)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (h->dflag) cudaFree(h->dflag);
     for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c)
@@ -303,6 +330,10 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     P.rc.ticket = nullptr;
     P.rc.st = nullptr;
     P.rc.stage = ST_NONE;
+    P.nrhs = 1;
+    P.vs = 0;
+    P.guard = nullptr;
+    P.guard_kind = GUARD_NONE;
     const double k = h->kappa;
     auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y) {
         P.parity = parity;

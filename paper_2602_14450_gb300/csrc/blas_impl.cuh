@@ -18,14 +18,22 @@ __device__ __forceinline__ void cscale_add(C& or_, C& oi, C ar, C ai, C vr, C vi
 
 #define GRID_STRIDE(h, n) for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < (n); h += gridDim.x * blockDim.x)
 
+// Per right-hand-side loop over the sites of a batched launch.
+#define RHS_LOOP(h, n) for (int h = sl.b * blockDim.x + threadIdx.x; h < (n); h += sl.nb * blockDim.x)
+
 // p := r (first iteration) or cP p - cV v + r
 template <typename T>
-__global__ void __launch_bounds__(256) k_pupdate(int n, uint4* p, const uint4* v, const uint4* r, const SolverState* st) {
+__global__ void __launch_bounds__(256) k_pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v,
+                                                 const uint4* r, const SolverState* sts) {
     typedef typename Unit<T>::C C;
-    if (solve_done(st)) return;
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_INNER)) return;
+    const long long ro = sl.rhs * vs;
+    p += ro; v += ro; r += ro;
     const bool first = st->first;
     const C pr = (C)st->cP[0], pi = (C)st->cP[1], vr = (C)st->cV[0], vi = (C)st->cV[1];
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         C rr[24], o[24];
         load_spinor<T>(r, n, h, rr);
         if (first) {
@@ -50,11 +58,16 @@ __global__ void __launch_bounds__(256) k_pupdate(int n, uint4* p, const uint4* v
 
 // r := r - alpha v
 template <typename T>
-__global__ void __launch_bounds__(256) k_supdate(int n, uint4* r, const uint4* v, const SolverState* st) {
+__global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v,
+                                                 const SolverState* sts) {
     typedef typename Unit<T>::C C;
-    if (solve_done(st)) return;
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_INNER)) return;
+    const long long o = sl.rhs * vs;
+    r += o; v += o;
     const C ar = (C)-st->alpha[0], ai = (C)-st->alpha[1];
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         C rr[24], vv[24];
         load_spinor<T>(r, n, h, rr);
         load_spinor<T>(v, n, h, vv);
@@ -68,15 +81,19 @@ __global__ void __launch_bounds__(256) k_supdate(int n, uint4* r, const uint4* v
 // r := r - omega t
 // sums: |r|^2, |x|^2, (r*, r) [the last only when WITH_RS]
 template <typename T, bool WITH_RS>
-__global__ void __launch_bounds__(256) k_xr(int n, uint4* x, uint4* r, const uint4* p, const uint4* t,
-                                            const uint4* rstar, SolverState* st, RedCtx rc) {
+__global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
+                                            const uint4* t, const uint4* rstar, SolverState* sts, RedCtx rc) {
     typedef typename Unit<T>::C C;
-    if (solve_done(st)) return;
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_INNER)) return;
+    const long long o = sl.rhs * vs;
+    x += o; r += o; p += o; t += o; rstar += o;
     const bool first = st->first;
     const C xr_r = (C)st->cXr[0], xr_i = (C)st->cXr[1], xp_r = (C)st->cXp[0], xp_i = (C)st->cXp[1];
     const C om_r = (C)-st->omega[0], om_i = (C)-st->omega[1];
     C s_r2 = 0, s_x2 = 0, s_re = 0, s_im = 0;
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         C rr[24], pp[24], xx[24], tt[24];
         load_spinor<T>(r, n, h, rr);
         load_spinor<T>(p, n, h, pp);
@@ -112,20 +129,25 @@ __global__ void __launch_bounds__(256) k_xr(int n, uint4* x, uint4* r, const uin
         }
     }
     double v[4] = {(double)s_r2, (double)s_x2, (double)s_re, (double)s_im};
-    grid_reduce<4>(v, rc);
+    grid_reduce<4>(v, rc, sl);
 }
 
 // r := (sigma / g) r, and x := lambda x when rescaling the solution (Alg. 4)
 // sums: |r|^2, (r*, r)
 template <typename T>
-__global__ void __launch_bounds__(256) k_scale(int n, uint4* r, uint4* x, const uint4* rstar, SolverState* st, RedCtx rc) {
+__global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, uint4* r, uint4* x,
+                                               const uint4* rstar, SolverState* sts, RedCtx rc) {
     typedef typename Unit<T>::C C;
-    if (solve_done(st)) return;
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_INNER)) return;
+    const long long o = sl.rhs * vs;
+    r += o; x += o; rstar += o;
     const C gs = (C)st->gam_tmp;
     const bool resx = st->rescale_x;
     const C lam = (C)st->lam;
     C s_r2 = 0, s_re = 0, s_im = 0;
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         C rr[24], rs[24];
         load_spinor<T>(r, n, h, rr);
 #pragma unroll
@@ -147,7 +169,7 @@ __global__ void __launch_bounds__(256) k_scale(int n, uint4* r, uint4* x, const 
         }
     }
     double v[3] = {(double)s_r2, (double)s_re, (double)s_im};
-    grid_reduce<3>(v, rc);
+    grid_reduce<3>(v, rc, sl);
 }
 
 // Rescale the FP64 outer residual and demote it (Alg. 2, first lines):
@@ -180,14 +202,20 @@ __device__ __forceinline__ const T* elem_ptr(const uint4* base, int stride, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rescale_in(int n, const uint4* r64, uint4* r, uint4* rstar, int ftz,
-                                                    SolverState* st, RedCtx rc) {
+__global__ void __launch_bounds__(256) k_rescale_in(int n, int nrhs, long long vs, long long vs64, const uint4* r64,
+                                                    uint4* r, uint4* rstar, int ftz, SolverState* sts, RedCtx rc) {
     typedef typename Unit<T>::C C;
     constexpr int N = Unit<T>::N;
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_OUTER)) return;
+    r64 += sl.rhs * vs64;
+    r += sl.rhs * vs;
+    rstar += sl.rhs * vs;
     const double f = st->s / st->rnorm;
     C s_n2 = 0;
     double nz = 0;
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         double src[24];
         load_spinor<double>(r64, n, h, src);
         alignas(16) T y[24];
@@ -211,14 +239,20 @@ __global__ void __launch_bounds__(256) k_rescale_in(int n, const uint4* r64, uin
         }
     }
     double v[2] = {(double)s_n2, nz};
-    grid_reduce<2>(v, rc);
+    grid_reduce<2>(v, rc, sl);
 }
 
 // x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 2 correction; Alg. 1: s^ -> s)
 template <typename T>
-__global__ void __launch_bounds__(256) k_correct(int n, uint4* x64, const uint4* xt, const SolverState* st) {
+__global__ void __launch_bounds__(256) k_correct(int n, int nrhs, long long vs, long long vs64, uint4* x64,
+                                                 const uint4* xt, const SolverState* sts) {
+    const Slice sl = slice_of(nrhs);
+    const SolverState* st = sts + sl.rhs;
+    if (guarded(st, GUARD_OUTER)) return;
+    x64 += sl.rhs * vs64;
+    xt += sl.rhs * vs;
     const double f = st->rnorm / (st->use_shat ? st->shat : st->s) / st->lambda_p;
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
 #pragma unroll
         for (int e = 0; e < 24; ++e) {
             double* xp = elem_ptr<double>(x64, n, h, e);
@@ -229,17 +263,20 @@ __global__ void __launch_bounds__(256) k_correct(int n, uint4* x64, const uint4*
 
 // sum |v|^2 over a packed vector; stage as given (ST_ACC / ST_ACC_SET / ST_OUTER)
 template <typename T>
-__global__ void __launch_bounds__(256) k_norm2(int n, const uint4* v, RedCtx rc) {
+__global__ void __launch_bounds__(256) k_norm2(int n, int nrhs, long long vs, const uint4* v, RedCtx rc, int gk) {
     typedef typename Unit<T>::C C;
+    const Slice sl = slice_of(nrhs);
+    if (guarded(rc.st ? rc.st + sl.rhs : nullptr, gk)) return;
+    v += sl.rhs * vs;
     C s = 0;
-    GRID_STRIDE(h, n) {
+    RHS_LOOP(h, n) {
         C a[24];
         load_spinor<T>(v, n, h, a);
 #pragma unroll
         for (int i = 0; i < 24; ++i) s += a[i] * a[i];
     }
     double d[1] = {(double)s};
-    grid_reduce<1>(d, rc);
+    grid_reduce<1>(d, rc, sl);
 }
 
 // lex FP64 (24 doubles per site) -> packed parity vector of T
@@ -293,5 +330,6 @@ __global__ void k_build_links(Geom g, int parity, const double* U, uint4* out) {
 }
 
 #undef GRID_STRIDE
+#undef RHS_LOOP
 
 }  // namespace wd

@@ -182,6 +182,7 @@ struct SolverState {
     double sigma, sigma_lambda, eps, omega0;
     int recalc, rescale_x, max_matvecs, scale_pass;
     int iter, matvecs, first, done, status;
+    int skip;                       // right-hand side finished: every kernel leaves it alone
     // refinement (outer) scalars
     double rnorm;                   // |b^ - A x| of the FP64 outer residual
     double shat;                    // |single(y~)|
@@ -353,13 +354,32 @@ __device__ inline void run_stage(int stage, const double* s, SolverState* st) {
 
 // Context of a reducing kernel: each block writes its partial sums; the
 // last block to finish (ticket) adds them in block order (deterministic),
-// runs the scalar stage and re-arms the ticket.
+// runs the scalar stage and re-arms the ticket. Arrays are indexed by the
+// right-hand side: partials[rhs][block][sum] (RED_STRIDE doubles per rhs),
+// ticket[rhs], st[rhs].
 struct RedCtx {
-    double* partials;    // [gridDim.x][NSUM]
+    double* partials;
     unsigned* ticket;    // zero between kernels
     SolverState* st;
     int stage;
 };
+
+// Partial-sum slots per right-hand side (blocks x sums).
+constexpr int RED_STRIDE = 8192 * 4;
+
+// A launch serves `nrhs` right-hand sides: block b works for rhs b % nrhs as
+// its (b / nrhs)-th block, so blocks that run together share site blocks
+// (and therefore links) across right-hand sides.
+struct Slice {
+    int rhs, b, nb;
+};
+__device__ __forceinline__ Slice slice_of(int nrhs) {
+    Slice s;
+    s.rhs = blockIdx.x % nrhs;
+    s.b = blockIdx.x / nrhs;
+    s.nb = gridDim.x / nrhs;
+    return s;
+}
 
 template <int NSUM>
 __device__ __forceinline__ void warp_sum(double (&v)[NSUM]) {
@@ -389,15 +409,18 @@ __device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
     }
 }
 
+// Reduce v over the sl.nb blocks that serve right-hand side sl.rhs.
 template <int NSUM>
-__device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc) {
+__device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc, const Slice& sl) {
     __shared__ unsigned is_last;
+    double* part = rc.partials + (size_t)sl.rhs * RED_STRIDE;
+    unsigned* ticket = rc.ticket + sl.rhs;
     block_sum<NSUM>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NSUM; ++k) rc.partials[(size_t)blockIdx.x * NSUM + k] = v[k];
+        for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = v[k];
         __threadfence();
-        is_last = (atomicAdd(rc.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+        is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
     }
     __syncthreads();
     if (!is_last) return;
@@ -405,19 +428,26 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc)
     double acc[NSUM];
 #pragma unroll
     for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < sl.nb; b += blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < NSUM; ++k) acc[k] += __ldcg(rc.partials + (size_t)b * NSUM + k);
+        for (int k = 0; k < NSUM; ++k) acc[k] += __ldcg(part + (size_t)b * NSUM + k);
     }
     block_sum<NSUM>(acc);
     if (threadIdx.x == 0) {
-        if (rc.st) run_stage(rc.stage, acc, rc.st);
-        *rc.ticket = 0u;
+        if (rc.st) run_stage(rc.stage, acc, rc.st + sl.rhs);
+        *ticket = 0u;
         __threadfence();
     }
 }
 
-// Early exit of every kernel of an inner iteration once the solve is done.
-__device__ __forceinline__ bool solve_done(const SolverState* st) { return st != nullptr && *(volatile const int*)&st->done; }
+// Guards: inner-loop kernels return once the inner solve of their right-hand
+// side is done (or the right-hand side is finished); refinement kernels only
+// skip finished right-hand sides.
+enum GuardKind { GUARD_NONE = 0, GUARD_INNER = 1, GUARD_OUTER = 2 };
+__device__ __forceinline__ bool guarded(const SolverState* st, int kind) {
+    if (st == nullptr || kind == GUARD_NONE) return false;
+    const volatile SolverState* v = st;
+    return v->skip || (kind == GUARD_INNER && v->done);
+}
 
 }  // namespace wd

@@ -5,18 +5,27 @@
 #include <cstdio>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "../../include/wd.h"
 #include "kernels.h"
 
 struct GraphKey {
-    int prec, recon, scale_pass, iters;
+    int prec, recon, scale_pass, iters, nrhs;
+    long long gen;
     bool operator<(const GraphKey& o) const {
         if (prec != o.prec) return prec < o.prec;
         if (recon != o.recon) return recon < o.recon;
         if (scale_pass != o.scale_pass) return scale_pass < o.scale_pass;
-        return iters < o.iters;
+        if (iters != o.iters) return iters < o.iters;
+        if (nrhs != o.nrhs) return nrhs < o.nrhs;
+        return gen < o.gen;
     }
+};
+
+struct Buffer {
+    void* p = nullptr;
+    size_t bytes = 0;
 };
 
 struct wd_handle {
@@ -30,12 +39,15 @@ struct wd_handle {
     double unit_dev = -1.0, det_dev = -1.0;
     uint4* links[4][2][2] = {};        // [prec][recon 12 -> 0, 18 -> 1][output parity]
 
-    std::map<std::string, void*> ws;   // named device workspaces
-    wd::SolverState* st = nullptr;     // device scalar state of wd_solve
+    std::map<std::string, Buffer> ws; // named device workspaces
+    long long gen = 0;                 // bumped whenever a workspace moves
+    int cap_rhs = 0;                   // right-hand sides the state arrays hold
+    wd::SolverState* st = nullptr;     // device scalar state, one per right-hand side
     wd::SolverState* hst = nullptr;    // pinned host mirror
-    int* hflag = nullptr;              // pinned: done flags of in-flight graph launches
-    double* partials = nullptr;        // reduction partials
-    unsigned* ticket = nullptr;        // reduction ticket
+    int* dflag = nullptr;              // device: "some right-hand side still iterating"
+    int* hflag = nullptr;              // pinned: copies of dflag of in-flight graph launches
+    double* partials = nullptr;        // reduction partials, RED_STRIDE per right-hand side
+    unsigned* ticket = nullptr;        // reduction tickets, one per right-hand side
     cudaStream_t cap = nullptr;        // capture stream
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -46,8 +58,10 @@ namespace wd {
 
 int fail(wd_handle* h, int code, const char* fmt, ...);
 int cuda_fail(wd_handle* h, cudaError_t e, const char* what);
+// Device buffer `name` of at least `bytes` (reallocated, and gen bumped, when too small).
 void* workspace(wd_handle* h, const std::string& name, size_t bytes);
-int ensure_solver_state(wd_handle* h);
+// Scalar state, partials and tickets for `nrhs` right-hand sides.
+int ensure_solver_state(wd_handle* h, int nrhs);
 int ensure_links(wd_handle* h, int prec, int recon, const uint4** even, const uint4** odd);
 size_t vec_bytes(const wd_handle* h, int prec);
 RedCtx red_ctx(wd_handle* h, int stage);

@@ -223,7 +223,14 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
     constexpr float SC = Wide<T>::SCALE;
-    if (solve_done(P.guard)) return;
+    const Slice sl = slice_of(P.nrhs);
+    if (guarded(P.guard ? P.guard + sl.rhs : nullptr, P.guard_kind)) return;
+    const long long ro = (long long)sl.rhs * P.vs;     // this right-hand side's vectors
+    const uint4* __restrict__ vin = P.in + ro;
+    uint4* vout = P.out + ro;
+    const uint4* vy = P.y ? P.y + ro : nullptr;
+    const uint4* vz = P.z ? P.z + ro : nullptr;
+    const uint4* vrs = P.rstar ? P.rstar + ro : nullptr;
 
     const Geom& g = P.g;
     const int p = P.parity;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) part[k] = 0.f;
 
-    for (int ha = blockIdx.x * blockDim.x + threadIdx.x; ha < half; ha += gridDim.x * blockDim.x) {
+    for (int ha = sl.b * blockDim.x + threadIdx.x; ha < half; ha += sl.nb * blockDim.x) {
         const int hb = ha + half;
         const int row = ha / Lxh;
         const int xh = ha - row * Lxh;
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
                 const float pha = (wa && g.bc[mu] < 0) ? -SC : SC;
                 const float phb = (wb && g.bc[mu] < 0) ? -SC : SC;
                 float2 nbp[24];
-                load_pair<T>(P.in, Vh, na, nb, nbp);
+                load_pair<T>(vin, Vh, na, nb, nbp);
                 float2 hs[12], chi[12];
                 project2(mu, fwd, nbp, f2(pha, phb), hs);
                 link_mul2<T, R>(la, lb, j * R, hs, chi);
@@ -309,21 +316,21 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
         for (int i = 0; i < 24; ++i) o[i] = mul2(A2, acc[i]);
         float2 yv[24];
         if constexpr (EPI >= EPI_Y) {
-            load_pair<T>(P.y, Vh, ha, hb, yv);
+            load_pair<T>(vy, Vh, ha, hb, yv);
 #pragma unroll
             for (int i = 0; i < 24; ++i) o[i] = fma2(B2, yv[i], o[i]);
         }
         if constexpr (EPI >= EPI_YZ) {
             float2 zv[24];
-            load_pair<T>(P.z, Vh, ha, hb, zv);
+            load_pair<T>(vz, Vh, ha, hb, zv);
 #pragma unroll
             for (int i = 0; i < 24; ++i) o[i] = fma2(C2, zv[i], o[i]);
         }
-        store_pair<T>(P.out, Vh, ha, hb, o);
+        store_pair<T>(vout, Vh, ha, hb, o);
 
         if constexpr (RED == RED_RSV) {
             float2 rs[24];
-            load_pair<T>(P.rstar, Vh, ha, hb, rs);
+            load_pair<T>(vrs, Vh, ha, hb, rs);
 #pragma unroll
             for (int i = 0; i < 12; ++i) {   // conj(rs) * o, both sites
                 const float2 rr = mul2(rs[2 * i], SC2), ri = mul2(rs[2 * i + 1], SC2);
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
         double v[NS];
 #pragma unroll
         for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc);
+        grid_reduce<NS>(v, P.rc, sl);
     }
 }
 

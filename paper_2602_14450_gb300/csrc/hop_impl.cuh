@@ -147,7 +147,14 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
-    if (solve_done(P.guard)) return;
+    const Slice sl = slice_of(P.nrhs);
+    if (guarded(P.guard ? P.guard + sl.rhs : nullptr, P.guard_kind)) return;
+    const long long ro = (long long)sl.rhs * P.vs;     // this right-hand side's vectors
+    const uint4* __restrict__ vin = P.in + ro;
+    uint4* vout = P.out + ro;
+    const uint4* vy = P.y ? P.y + ro : nullptr;
+    const uint4* vz = P.z ? P.z + ro : nullptr;
+    const uint4* vrs = P.rstar ? P.rstar + ro : nullptr;
 
     const Geom& g = P.g;
     const int p = P.parity;
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) part[k] = 0;
 
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+    for (int h = sl.b * blockDim.x + threadIdx.x; h < Vh; h += sl.nb * blockDim.x) {
         const int row = h / Lxh;
         const int xh = h - row * Lxh;
         const int y = row % Ly;
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
                     hn = fwd ? (wrap ? h - (Lt - 1) * st : h + st) : (wrap ? h + (Lt - 1) * st : h - st);
                 }
                 C nb[24];
-                load_spinor<T>(P.in, Vh, hn, nb);
+                load_spinor<T>(vin, Vh, hn, nb);
                 C hs[12], chi[12];
                 project<C>(mu, fwd, nb, hs);
                 if (wrap && g.bc[mu] < 0) {
@@ -217,21 +224,21 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
         for (int i = 0; i < 24; ++i) o[i] = ca * acc[i];
         C yv[24];
         if constexpr (EPI >= EPI_Y) {
-            load_spinor<T>(P.y, Vh, h, yv);
+            load_spinor<T>(vy, Vh, h, yv);
 #pragma unroll
             for (int i = 0; i < 24; ++i) o[i] += cb * yv[i];
         }
         if constexpr (EPI >= EPI_YZ) {
             C zv[24];
-            load_spinor<T>(P.z, Vh, h, zv);
+            load_spinor<T>(vz, Vh, h, zv);
 #pragma unroll
             for (int i = 0; i < 24; ++i) o[i] += cc * zv[i];
         }
-        store_spinor<T>(P.out, Vh, h, o);
+        store_spinor<T>(vout, Vh, h, o);
 
         if constexpr (RED == RED_RSV) {
             C rs[24];
-            load_spinor<T>(P.rstar, Vh, h, rs);
+            load_spinor<T>(vrs, Vh, h, rs);
 #pragma unroll
             for (int i = 0; i < 12; ++i) {   // conj(rs) * o
                 part[0] += rs[2 * i] * o[2 * i] + rs[2 * i + 1] * o[2 * i + 1];
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
         double v[NS];
 #pragma unroll
         for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc);
+        grid_reduce<NS>(v, P.rc, sl);
     }
 }
 

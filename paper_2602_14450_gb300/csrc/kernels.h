@@ -1,5 +1,11 @@
 // Host-side launchers of the device kernels, one instantiation per storage
 // type (translation units ops_f64.cu, ops_f32.cu, ops_f16.cu, ops_bf16.cu).
+//
+// Every vector argument may hold a batch of `nrhs` right-hand sides stored
+// back to back: right-hand side r of a packed parity vector starts `vs`
+// 16-byte units after right-hand side r - 1 (vs = units per site * V/2 for a
+// tightly packed batch). Scalar state, reduction partials and tickets are
+// arrays over right-hand sides (see RedCtx).
 #pragma once
 
 #include "common.cuh"
@@ -12,7 +18,9 @@ enum Red { RED_NONE = 0, RED_RSV = 1, RED_TS = 2, RED_NORM = 3 };
 struct HopParams {
     Geom g;
     int parity;             // parity of the output sites
-    const uint4* links;     // gathered links of the output parity
+    int nrhs;               // right-hand sides in the batch (>= 1)
+    long long vs;           // units between right-hand sides of every spinor argument
+    const uint4* links;     // gathered links of the output parity (shared by all rhs)
     const uint4* in;        // input spinor on parity 1 - parity
     uint4* out;             // output spinor on `parity`
     const uint4* y;         // epilogue operands on `parity`
@@ -20,29 +28,38 @@ struct HopParams {
     const uint4* rstar;     // RED_RSV: sum conj(rstar) out
     double a, b, c;         // out = a * H in + b * y + c * z
     RedCtx rc;              // reduction target (partials, ticket, state, stage)
-    const SolverState* guard;  // if set, return at once when guard->done (inner-loop kernels)
+    const SolverState* guard;  // per-rhs state consulted by the guard
+    int guard_kind;            // GuardKind
 };
 
-// Largest number of blocks any reducing kernel uses (partials capacity).
+// Largest number of blocks a reducing kernel uses per right-hand side.
 constexpr int MAX_RED_BLOCKS = 8192;
 constexpr int MAX_RED_SUMS = 4;
+static_assert(MAX_RED_BLOCKS * MAX_RED_SUMS == RED_STRIDE, "partials layout");
 
 // Units of 16 bytes per site of the gathered links of one parity.
 int link_units(int prec, int recon);
 // Units of 16 bytes per site of a spinor.
 int spinor_units(int prec);
 
+// Vector kernels: n = sites per parity, vs = units between right-hand sides
+// (vs64 for FP64 vectors), st = state array, g = guard kind.
 template <typename T> struct Ops {
     static cudaError_t hop(int recon, int epi, int red, const HopParams& P, cudaStream_t s);
-    static cudaError_t pupdate(int n, uint4* p, const uint4* v, const uint4* r, const SolverState* st, cudaStream_t s);
-    static cudaError_t supdate(int n, uint4* r, const uint4* v, const SolverState* st, cudaStream_t s);
-    static cudaError_t xr(bool with_rs, int n, uint4* x, uint4* r, const uint4* p, const uint4* t, const uint4* rstar,
-                          SolverState* st, RedCtx rc, cudaStream_t s);
-    static cudaError_t scale(int n, uint4* r, uint4* x, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s);
-    static cudaError_t rescale_in(int n, const uint4* r64, uint4* r, uint4* rstar, int ftz, SolverState* st, RedCtx rc,
-                                  cudaStream_t s);
-    static cudaError_t correct(int n, uint4* x64, const uint4* xt, const SolverState* st, cudaStream_t s);
-    static cudaError_t norm2(int n, const uint4* v, RedCtx rc, cudaStream_t s);
+    static cudaError_t pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v, const uint4* r,
+                               const SolverState* st, cudaStream_t s);
+    static cudaError_t supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
+                               cudaStream_t s);
+    static cudaError_t xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
+                          const uint4* t, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s);
+    static cudaError_t scale(int n, int nrhs, long long vs, uint4* r, uint4* x, const uint4* rstar, SolverState* st,
+                             RedCtx rc, cudaStream_t s);
+    static cudaError_t rescale_in(int n, int nrhs, long long vs, long long vs64, const uint4* r64, uint4* r,
+                                  uint4* rstar, int ftz, SolverState* st, RedCtx rc, cudaStream_t s);
+    static cudaError_t correct(int n, int nrhs, long long vs, long long vs64, uint4* x64, const uint4* xt,
+                               const SolverState* st, cudaStream_t s);
+    static cudaError_t norm2(int n, int nrhs, long long vs, const uint4* v, RedCtx rc, int guard_kind,
+                             cudaStream_t s);
     static cudaError_t pack(const Geom& g, int parity, const double* lex, uint4* out, cudaStream_t s);
     static cudaError_t unpack(const Geom& g, int parity, const uint4* in, double* lex, cudaStream_t s);
     static cudaError_t build_links(int recon, const Geom& g, int parity, const double* U, uint4* out, cudaStream_t s);
@@ -51,7 +68,7 @@ template <typename T> struct Ops {
 cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* out, cudaStream_t s);
 
 // Block size of every vector kernel; the hop kernels take theirs from
-// hop_block() (set by the tuner, default 128).
+// hop_block() (default 128).
 constexpr int VEC_BLOCK = 256;
 int hop_block();
 void set_hop_block(int b);

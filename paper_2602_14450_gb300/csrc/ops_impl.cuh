@@ -27,17 +27,18 @@ inline int blocks_per_sm(const void* kernel, int block) {
     return n;
 }
 
-// Grid of a reducing kernel: every block resident at once, no more blocks
-// than needed to cover n items, and at most MAX_RED_BLOCKS partial sums.
-inline int reduce_grid(const void* kernel, int n, int block) {
+// Blocks per right-hand side of a reducing kernel: every block of the launch
+// resident at once, no more blocks than needed to cover n items, and at most
+// MAX_RED_BLOCKS partial sums per right-hand side.
+inline int reduce_blocks(const void* kernel, int n, int block, int nrhs) {
     long need = ((long)n + block - 1) / block;
-    long g = (long)blocks_per_sm(kernel, block) * num_sms();
+    long g = (long)blocks_per_sm(kernel, block) * num_sms() / nrhs;
     if (g > need) g = need;
     if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
     return g < 1 ? 1 : (int)g;
 }
 
-inline int stream_grid(int n, int block) {
+inline int stream_blocks(int n, int block) {
     long g = ((long)n + block - 1) / block;
     return g < 1 ? 1 : (int)g;
 }
@@ -45,23 +46,25 @@ inline int stream_grid(int n, int block) {
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     const int block = hop_block();
+    const int nr = P.nrhs;
     if constexpr (!std::is_same<T, double>::value) {
         if (hop_variant() == 2) {   // two sites per thread, packed FP32x2 arithmetic
             const int n = P.g.Vh / 2;
             const void* k2 = (const void*)hop2_kernel<T, R, E, D>;
-            const int grid = (D == RED_NONE) ? stream_grid(n, block) : reduce_grid(k2, n, block);
-            hop2_kernel<T, R, E, D><<<grid, block, 0, s>>>(P);
+            const int nb = (D == RED_NONE) ? stream_blocks(n, block) : reduce_blocks(k2, n, block, nr);
+            hop2_kernel<T, R, E, D><<<nb * nr, block, 0, s>>>(P);
             return cudaGetLastError();
         }
     }
     const void* k = (const void*)hop_kernel<T, R, E, D>;
-    const int grid = (D == RED_NONE) ? stream_grid(P.g.Vh, block) : reduce_grid(k, P.g.Vh, block);
-    hop_kernel<T, R, E, D><<<grid, block, 0, s>>>(P);
+    const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
+    hop_kernel<T, R, E, D><<<nb * nr, block, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::hop(int recon, int epi, int red, const HopParams& P, cudaStream_t s) {
+    if (P.nrhs < 1) return cudaErrorInvalidValue;
 #define WD_HOP_CASE(R, E, D) \
     if (recon == R && epi == E && red == D) return run_hop<T, R, E, D>(P, s);
     WD_HOP_CASE(12, EPI_H, RED_NONE)
@@ -79,76 +82,81 @@ cudaError_t Ops<T>::hop(int recon, int epi, int red, const HopParams& P, cudaStr
 }
 
 template <typename T>
-cudaError_t Ops<T>::pupdate(int n, uint4* p, const uint4* v, const uint4* r, const SolverState* st, cudaStream_t s) {
-    k_pupdate<T><<<stream_grid(n, VEC_BLOCK), VEC_BLOCK, 0, s>>>(n, p, v, r, st);
+cudaError_t Ops<T>::pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v, const uint4* r,
+                            const SolverState* st, cudaStream_t s) {
+    k_pupdate<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, p, v, r, st);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::supdate(int n, uint4* r, const uint4* v, const SolverState* st, cudaStream_t s) {
-    k_supdate<T><<<stream_grid(n, VEC_BLOCK), VEC_BLOCK, 0, s>>>(n, r, v, st);
+cudaError_t Ops<T>::supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
+                            cudaStream_t s) {
+    k_supdate<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, r, v, st);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::xr(bool with_rs, int n, uint4* x, uint4* r, const uint4* p, const uint4* t, const uint4* rstar,
-                       SolverState* st, RedCtx rc, cudaStream_t s) {
+cudaError_t Ops<T>::xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
+                       const uint4* t, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s) {
     if (with_rs) {
-        const int g = reduce_grid((const void*)k_xr<T, true>, n, VEC_BLOCK);
-        k_xr<T, true><<<g, VEC_BLOCK, 0, s>>>(n, x, r, p, t, rstar, st, rc);
+        const int nb = reduce_blocks((const void*)k_xr<T, true>, n, VEC_BLOCK, nrhs);
+        k_xr<T, true><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, st, rc);
     } else {
-        const int g = reduce_grid((const void*)k_xr<T, false>, n, VEC_BLOCK);
-        k_xr<T, false><<<g, VEC_BLOCK, 0, s>>>(n, x, r, p, t, rstar, st, rc);
+        const int nb = reduce_blocks((const void*)k_xr<T, false>, n, VEC_BLOCK, nrhs);
+        k_xr<T, false><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, st, rc);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::scale(int n, uint4* r, uint4* x, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s) {
-    const int g = reduce_grid((const void*)k_scale<T>, n, VEC_BLOCK);
-    k_scale<T><<<g, VEC_BLOCK, 0, s>>>(n, r, x, rstar, st, rc);
+cudaError_t Ops<T>::scale(int n, int nrhs, long long vs, uint4* r, uint4* x, const uint4* rstar, SolverState* st,
+                          RedCtx rc, cudaStream_t s) {
+    const int nb = reduce_blocks((const void*)k_scale<T>, n, VEC_BLOCK, nrhs);
+    k_scale<T><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, r, x, rstar, st, rc);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::rescale_in(int n, const uint4* r64, uint4* r, uint4* rstar, int ftz, SolverState* st, RedCtx rc,
-                               cudaStream_t s) {
-    const int g = reduce_grid((const void*)k_rescale_in<T>, n, VEC_BLOCK);
-    k_rescale_in<T><<<g, VEC_BLOCK, 0, s>>>(n, r64, r, rstar, ftz, st, rc);
+cudaError_t Ops<T>::rescale_in(int n, int nrhs, long long vs, long long vs64, const uint4* r64, uint4* r,
+                               uint4* rstar, int ftz, SolverState* st, RedCtx rc, cudaStream_t s) {
+    const int nb = reduce_blocks((const void*)k_rescale_in<T>, n, VEC_BLOCK, nrhs);
+    k_rescale_in<T><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, vs64, r64, r, rstar, ftz, st, rc);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::correct(int n, uint4* x64, const uint4* xt, const SolverState* st, cudaStream_t s) {
-    k_correct<T><<<stream_grid(n, VEC_BLOCK), VEC_BLOCK, 0, s>>>(n, x64, xt, st);
+cudaError_t Ops<T>::correct(int n, int nrhs, long long vs, long long vs64, uint4* x64, const uint4* xt,
+                            const SolverState* st, cudaStream_t s) {
+    k_correct<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, vs64, x64, xt, st);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Ops<T>::norm2(int n, const uint4* v, RedCtx rc, cudaStream_t s) {
-    const int g = reduce_grid((const void*)k_norm2<T>, n, VEC_BLOCK);
-    k_norm2<T><<<g, VEC_BLOCK, 0, s>>>(n, v, rc);
+cudaError_t Ops<T>::norm2(int n, int nrhs, long long vs, const uint4* v, RedCtx rc, int guard_kind,
+                          cudaStream_t s) {
+    const int nb = reduce_blocks((const void*)k_norm2<T>, n, VEC_BLOCK, nrhs);
+    k_norm2<T><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, v, rc, guard_kind);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::pack(const Geom& g, int parity, const double* lex, uint4* out, cudaStream_t s) {
-    k_pack<T><<<stream_grid(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, lex, out);
+    k_pack<T><<<stream_blocks(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, lex, out);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::unpack(const Geom& g, int parity, const uint4* in, double* lex, cudaStream_t s) {
-    k_unpack<T><<<stream_grid(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, in, lex);
+    k_unpack<T><<<stream_blocks(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, in, lex);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::build_links(int recon, const Geom& g, int parity, const double* U, uint4* out, cudaStream_t s) {
     if (recon == 12)
-        k_build_links<T, 12><<<stream_grid(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, U, out);
+        k_build_links<T, 12><<<stream_blocks(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, U, out);
     else if (recon == 18)
-        k_build_links<T, 18><<<stream_grid(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, U, out);
+        k_build_links<T, 18><<<stream_blocks(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, U, out);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

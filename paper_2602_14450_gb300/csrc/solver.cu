@@ -1,16 +1,23 @@
-// wd_solve: FP64 iterative refinement (Alg. 1 / Alg. 2) around the rescaled
-// low-precision BiCGStab (Alg. 3 / Alg. 4) on the even-odd system of Eq. 4,
-// followed by the odd-site reconstruction of Eq. 5.
+// Solver driver: FP64 iterative refinement (Alg. 1 / Alg. 2) around the
+// rescaled low-precision BiCGStab (Alg. 3 / Alg. 4) on the even-odd system of
+// Eq. 4, followed by the odd-site reconstruction of Eq. 5, for a batch of
+// systems (lattices), each with one or more right-hand sides.
 //
 // Device-resident design: every scalar of the recurrences lives in a
-// SolverState in device memory and is updated by the last block of the
-// reducing kernel that produces its inputs; one inner BiCGStab iteration is
-// a fixed chain of 7-8 kernels captured once in a CUDA graph (several
-// iterations per graph). Kernels return immediately once the state says the
-// inner solve is done, so the host only polls a flag every few launches.
+// SolverState (one per right-hand side) in device memory and is updated by
+// the last block of the reducing kernel that produces its inputs. One inner
+// BiCGStab iteration of every system is a fixed chain of 7-8 kernels, each
+// launch covering all right-hand sides of a system (blocks of different
+// right-hand sides interleaved so that they share links through L2); several
+// iterations are captured in one CUDA graph. Kernels of a right-hand side
+// whose inner solve is done return at once; the host polls one flag per
+// graph launch, one launch behind. Right-hand sides that have converged in
+// the refinement loop are marked `skip` and every later kernel leaves them
+// alone.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "handle.h"
 
@@ -32,99 +39,174 @@ static bool scheme_cfg(int scheme, SchemeCfg* c) {
     }
 }
 
-// Low-precision work vectors of the inner solve (even sites unless noted).
-struct InnerVecs {
-    uint4 *r, *rs, *p, *v, *t, *x, *tmp;   // tmp: odd sites
+// Flag "some right-hand side of this system is still in its inner solve".
+__global__ void k_any_active(int nrhs, const SolverState* st, int* flag) {
+    const int r = threadIdx.x;
+    const bool act = r < nrhs && !st[r].done && !st[r].skip;
+    if (__syncthreads_or(act) && r == 0) *flag = 1;
+}
+
+// Device buffers of one system for one call.
+struct Sys {
+    wd_handle* h = nullptr;
+    int nrhs = 0;
+    const double* b = nullptr;
+    double* x = nullptr;
+    bool b_dev = true, x_dev = true;
+    double* bl = nullptr;       // device lexicographic sources (b or staging)
+    double* xl = nullptr;       // device lexicographic solutions (x or staging)
+    const uint4 *le64 = nullptr, *lo64 = nullptr, *le = nullptr, *lo = nullptr;
+    long long vs64 = 0, vs = 0; // units per right-hand side
+    uint4 *eta_e, *eta_o, *bhat, *x64, *r64, *tmp64, *xo;             // FP64, nrhs each
+    uint4 *r, *rs, *p, *v, *t, *xt, *tmp;                              // inner precision, nrhs each
+    std::vector<double> eta_norm;
+    std::vector<bool> active;
 };
 
-static int inner_vecs(wd_handle* h, int prec, InnerVecs* iv) {
-    const size_t b = vec_bytes(h, prec);
-    const std::string k = "in" + std::to_string(prec) + ".";
-    uint4** slots[7] = {&iv->r, &iv->rs, &iv->p, &iv->v, &iv->t, &iv->x, &iv->tmp};
-    const char* names[7] = {"r", "rs", "p", "v", "t", "x", "tmp"};
+static int prepare(Sys& S, int prec, int recon_lo) {
+    wd_handle* h = S.h;
+    int rc = ensure_solver_state(h, S.nrhs);
+    if (rc != WD_OK) return rc;
+    if ((rc = ensure_links(h, WD_FP64, 18, &S.le64, &S.lo64)) != WD_OK) return rc;
+    if ((rc = ensure_links(h, prec, recon_lo, &S.le, &S.lo)) != WD_OK) return rc;
+    const size_t b64 = vec_bytes(h, WD_FP64) * S.nrhs, blo = vec_bytes(h, prec) * S.nrhs;
+    S.vs64 = (long long)spinor_units(WD_FP64) * h->g.Vh;
+    S.vs = (long long)spinor_units(prec) * h->g.Vh;
+    uint4** f64[7] = {&S.eta_e, &S.eta_o, &S.bhat, &S.x64, &S.r64, &S.tmp64, &S.xo};
+    const char* n64[7] = {"eta_e", "eta_o", "bhat", "x", "r", "tmp", "xo"};
     for (int i = 0; i < 7; ++i) {
-        *slots[i] = (uint4*)workspace(h, k + names[i], b);
-        if (!*slots[i]) return fail(h, WD_ERR_CUDA, "out of device memory (%s)", names[i]);
+        *f64[i] = (uint4*)workspace(h, std::string("f64.") + n64[i], b64);
+        if (!*f64[i]) return fail(h, WD_ERR_CUDA, "out of device memory (%s)", n64[i]);
     }
+    uint4** flo[7] = {&S.r, &S.rs, &S.p, &S.v, &S.t, &S.xt, &S.tmp};
+    const char* nlo[7] = {"r", "rs", "p", "v", "t", "x", "tmp"};
+    const std::string pre = "in" + std::to_string(prec) + ".";
+    for (int i = 0; i < 7; ++i) {
+        *flo[i] = (uint4*)workspace(h, pre + nlo[i], blo);
+        if (!*flo[i]) return fail(h, WD_ERR_CUDA, "out of device memory (%s)", nlo[i]);
+    }
+    const size_t lexb = (size_t)S.nrhs * 2 * h->g.Vh * 24 * sizeof(double);
+    S.bl = const_cast<double*>(S.b);
+    S.xl = S.x;
+    if (!S.b_dev || !S.x_dev) {
+        double* stage = (double*)workspace(h, "lex.stage", lexb);
+        if (!stage) return fail(h, WD_ERR_CUDA, "out of device memory");
+        if (!S.b_dev) S.bl = stage;
+        if (!S.x_dev) S.xl = stage;   // b is consumed (packed) before x is written
+    }
+    S.eta_norm.assign(S.nrhs, 0.0);
+    S.active.assign(S.nrhs, false);
     return WD_OK;
 }
 
-// Enqueue one inner BiCGStab iteration (Alg. 3 / Alg. 4 loop body).
-static cudaError_t enqueue_iteration(wd_handle* h, int prec, int recon, bool scale_pass, const InnerVecs& iv,
-                                     const uint4* le, const uint4* lo, cudaStream_t s) {
-    const int n = h->g.Vh;
-    const double k2 = h->kappa * h->kappa;
-    SolverState* st = h->st;
+static HopParams hop_params(const Sys& S, int stage, int guard_kind) {
+    HopParams P{};
+    P.g = S.h->g;
+    P.nrhs = S.nrhs;
+    P.rc = red_ctx(S.h, stage);
+    P.guard = S.h->st;
+    P.guard_kind = guard_kind;
+    return P;
+}
+
+// One FP64 hop over all right-hand sides of a system.
+static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, int epi, int red, double a,
+                         const uint4* y, double b, const uint4* z, double c, int stage, int guard_kind,
+                         cudaStream_t s) {
+    HopParams P = hop_params(S, stage, guard_kind);
+    P.vs = S.vs64;
+    P.parity = parity;
+    P.links = parity == 0 ? S.le64 : S.lo64;
+    P.in = in;
+    P.out = out;
+    P.y = y;
+    P.z = z;
+    P.a = a;
+    P.b = b;
+    P.c = c;
+    return Ops<double>::hop(18, epi, red, P, s);
+}
+
+// Enqueue one inner BiCGStab iteration (Alg. 3 / Alg. 4 loop body) of every
+// right-hand side of a system.
+static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool scale_pass, cudaStream_t s) {
+    const int n = S.h->g.Vh, nr = S.nrhs;
+    const long long vs = S.vs;
+    const double k2 = S.h->kappa * S.h->kappa;
+    SolverState* st = S.h->st;
+    wd_handle* h = S.h;
     return by_prec(prec, [&](auto tag) -> cudaError_t {
         typedef typename decltype(tag)::type T;
         cudaError_t e;
-        HopParams P{};
-        P.g = h->g;
-        P.rc = red_ctx(h, ST_NONE);
-        P.guard = st;
+        HopParams P = hop_params(S, ST_NONE, GUARD_INNER);
+        P.vs = vs;
         // p := beta (p - omega' v) + r   (gamma of p and v folded in)
-        if ((e = Ops<T>::pupdate(n, iv.p, iv.v, iv.r, st, s)) != cudaSuccess) return e;
+        if ((e = Ops<T>::pupdate(n, nr, vs, S.p, S.v, S.r, st, s)) != cudaSuccess) return e;
         // v = A p = p - kappa^2 H_eo H_oe p ; alpha = rho / (r*, v)
-        P.parity = 1; P.links = lo; P.in = iv.p; P.out = iv.tmp; P.a = 1.0;
+        P.parity = 1; P.links = S.lo; P.in = S.p; P.out = S.tmp; P.a = 1.0;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = le; P.in = iv.tmp; P.out = iv.v; P.y = iv.p; P.a = -k2; P.b = 1.0;
-        P.rstar = iv.rs; P.rc = red_ctx(h, ST_ALPHA);
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.v; P.y = S.p; P.a = -k2; P.b = 1.0;
+        P.rstar = S.rs; P.rc = red_ctx(h, ST_ALPHA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_RSV, P, s)) != cudaSuccess) return e;
         // r := r - alpha v
-        if ((e = Ops<T>::supdate(n, iv.r, iv.v, st, s)) != cudaSuccess) return e;
+        if ((e = Ops<T>::supdate(n, nr, vs, S.r, S.v, st, s)) != cudaSuccess) return e;
         // t = A r ; omega from (t, r), (t, t), (r, r)
         P.rc = red_ctx(h, ST_NONE);
-        P.parity = 1; P.links = lo; P.in = iv.r; P.out = iv.tmp; P.y = nullptr; P.a = 1.0; P.b = 0.0; P.rstar = nullptr;
+        P.parity = 1; P.links = S.lo; P.in = S.r; P.out = S.tmp; P.y = nullptr; P.a = 1.0; P.b = 0.0;
+        P.rstar = nullptr;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = le; P.in = iv.tmp; P.out = iv.t; P.y = iv.r; P.a = -k2; P.b = 1.0;
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.t; P.y = S.r; P.a = -k2; P.b = 1.0;
         P.rc = red_ctx(h, ST_OMEGA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_TS, P, s)) != cudaSuccess) return e;
         // x += lambda'/gamma' (omega r + alpha p) ; r := r - omega t ; |r|, |x|
-        if ((e = Ops<T>::xr(!scale_pass, n, iv.x, iv.r, iv.p, iv.t, iv.rs, st, red_ctx(h, ST_RNORM), s)) != cudaSuccess)
+        if ((e = Ops<T>::xr(!scale_pass, n, nr, vs, S.xt, S.r, S.p, S.t, S.rs, st, red_ctx(h, ST_RNORM), s)) !=
+            cudaSuccess)
             return e;
         // r := (sigma / g) r ; gamma ; [x := lambda x] ; next rho, beta
         if (scale_pass)
-            if ((e = Ops<T>::scale(n, iv.r, iv.x, iv.rs, st, red_ctx(h, ST_END), s)) != cudaSuccess) return e;
+            if ((e = Ops<T>::scale(n, nr, vs, S.r, S.xt, S.rs, st, red_ctx(h, ST_END), s)) != cudaSuccess) return e;
         return cudaSuccess;
     });
 }
 
-static int inner_graph(wd_handle* h, int prec, int recon, bool scale_pass, int iters, const InnerVecs& iv,
-                       const uint4* le, const uint4* lo, cudaGraphExec_t* out) {
-    GraphKey key{prec, recon, scale_pass ? 1 : 0, iters};
-    auto it = h->graphs.find(key);
-    if (it != h->graphs.end()) {
-        *out = it->second;
-        return WD_OK;
-    }
+// Capture `iters` iterations of every system plus the activity flag.
+static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_pass, int iters,
+                         cudaGraphExec_t* out) {
+    wd_handle* h0 = sys[0].h;
     cudaGraph_t graph = nullptr;
-    WD_CUDA(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    WD_CUDA(h0, cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < iters && e == cudaSuccess; ++i) e = enqueue_iteration(h, prec, recon, scale_pass, iv, le, lo, h->cap);
-    cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+    for (int i = 0; i < iters && e == cudaSuccess; ++i)
+        for (auto& S : sys)
+            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, scale_pass, h0->cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h0->dflag, 0, sizeof(int), h0->cap);
+    for (auto& S : sys) {
+        if (e != cudaSuccess) break;
+        k_any_active<<<1, 1024, 0, h0->cap>>>(S.nrhs, S.h->st, h0->dflag);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h0->cap, &graph);
     if (e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(h, e, "capture of the inner iteration");
+        return cuda_fail(h0, e, "capture of the inner iteration");
     }
-    WD_CUDA(h, e2);
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    WD_CUDA(h0, e2);
+    e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
-    WD_CUDA(h, e);
-    h->graphs[key] = exec;
-    *out = exec;
+    WD_CUDA(h0, e);
     return WD_OK;
 }
 
-// Read the device state into the pinned mirror (synchronizes s).
-static int read_state(wd_handle* h, cudaStream_t s) {
-    WD_CUDA(h, cudaMemcpyAsync(h->hst, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-    WD_CUDA(h, cudaStreamSynchronize(s));
+static int read_states(std::vector<Sys>& sys, cudaStream_t s) {
+    for (auto& S : sys)
+        WD_CUDA(S.h, cudaMemcpyAsync(S.h->hst, S.h->st, sizeof(SolverState) * S.nrhs, cudaMemcpyDeviceToHost, s));
+    WD_CUDA(sys[0].h, cudaStreamSynchronize(s));
     return WD_OK;
 }
 
-static int write_state(wd_handle* h, cudaStream_t s) {
-    WD_CUDA(h, cudaMemcpyAsync(h->st, h->hst, sizeof(SolverState), cudaMemcpyHostToDevice, s));
+static int write_states(std::vector<Sys>& sys, cudaStream_t s) {
+    for (auto& S : sys)
+        WD_CUDA(S.h, cudaMemcpyAsync(S.h->st, S.h->hst, sizeof(SolverState) * S.nrhs, cudaMemcpyHostToDevice, s));
     return WD_OK;
 }
 
@@ -135,6 +217,250 @@ static bool is_device_ptr(const void* p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The driver behind wd_solve and wd_solve_batch.
+int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* const* b, double* const* x, double tol,
+                  int scheme, const wd_solve_params* params, wd_solve_stats* stats, cudaStream_t s) {
+    wd_handle* h0 = hs[0];
+    SchemeCfg cfg;
+    if (!(tol > 0) || !scheme_cfg(scheme, &cfg)) return fail(h0, WD_ERR_INVALID_ARG, "bad tolerance or scheme");
+    wd_solve_params prm;
+    if (params) prm = *params; else wd_solve_params_default(scheme, &prm);
+    if (!valid_recon(prm.recon) || prm.max_outer < 1 || prm.max_inner < 2 || !(prm.s > 0) || prm.sigma < 0 ||
+        prm.iters_per_sync < 1 || (prm.rescale_x && !(prm.sigma_lambda > 0)))
+        return fail(h0, WD_ERR_INVALID_ARG, "bad solver parameters");
+    const int prec = cfg.prec;
+    const int recon_lo = cfg.fp64_inner ? 18 : prm.recon;
+    const bool scale_pass = prm.sigma > 0 || prm.rescale_x;
+    const int ips = prm.iters_per_sync;
+    const int kpi = scale_pass ? 8 : 7;   // kernels per inner iteration
+
+    std::vector<Sys> sys;
+    int total_rhs = 0;
+    for (int i = 0; i < n; ++i) {
+        if (nrhs[i] == 0) continue;
+        Sys S;
+        S.h = hs[i];
+        S.nrhs = nrhs[i];
+        S.b = b[i];
+        S.x = x[i];
+        if (!S.h->have_gauge) return fail(S.h, WD_ERR_NO_GAUGE, "wd_set_gauge has not been called");
+        for (auto& o : sys)
+            if (o.h == S.h) return fail(S.h, WD_ERR_INVALID_ARG, "a handle appears twice in one batch");
+        S.b_dev = is_device_ptr(S.b);
+        S.x_dev = is_device_ptr(S.x);
+        int rc = prepare(S, prec, recon_lo);
+        if (rc != WD_OK) return rc;
+        sys.push_back(S);
+        total_rhs += S.nrhs;
+    }
+    if (sys.empty()) return WD_OK;
+    if (total_rhs > 1024) return fail(h0, WD_ERR_INVALID_ARG, "at most 1024 right-hand sides per call");
+
+    long long nk = 0;   // kernels launched by this call
+    std::vector<wd_solve_stats> out(total_rhs);
+    WD_CUDA(h0, cudaEventRecord(h0->t0, s));
+    // Eq. 4 right-hand side b^ = eta_e + kappa H_eo eta_o, |eta|^2, and r = b^ - A x
+    for (auto& S : sys) {
+        wd_handle* h = S.h;
+        const int nv = h->g.Vh;
+        const size_t len = (size_t)2 * nv * 24;
+        const size_t lexb = S.nrhs * len * sizeof(double);
+        if (!S.b_dev) WD_CUDA(h, cudaMemcpyAsync(S.bl, S.b, lexb, cudaMemcpyHostToDevice, s));
+        for (int r = 0; r < S.nrhs; ++r) {
+            WD_CUDA(h, Ops<double>::pack(h->g, 0, S.bl + r * len, S.eta_e + r * S.vs64, s));
+            WD_CUDA(h, Ops<double>::pack(h->g, 1, S.bl + r * len, S.eta_o + r * S.vs64, s));
+        }
+        for (int r = 0; r < S.nrhs; ++r) h->hst[r].skip = 0;
+        WD_CUDA(h, cudaMemcpyAsync(h->st, h->hst, sizeof(SolverState) * S.nrhs, cudaMemcpyHostToDevice, s));
+        WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_e, red_ctx(h, ST_ACC_SET), GUARD_NONE, s));
+        WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_o, red_ctx(h, ST_ACC), GUARD_NONE, s));
+        WD_CUDA(h, hop64(S, 0, S.eta_o, S.bhat, EPI_Y, RED_NONE, h->kappa, S.eta_e, 1.0, nullptr, 0.0, ST_NONE,
+                         GUARD_NONE, s));
+        nk += 2 * S.nrhs + 3;
+        if (prm.x_is_guess) {
+            if (!S.x_dev) WD_CUDA(h, cudaMemcpyAsync(S.xl, S.x, lexb, cudaMemcpyHostToDevice, s));
+            for (int r = 0; r < S.nrhs; ++r)
+                WD_CUDA(h, Ops<double>::pack(h->g, 0, S.xl + r * len, S.x64 + r * S.vs64, s));
+            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE,
+                             GUARD_NONE, s));
+            WD_CUDA(h, hop64(S, 0, S.tmp64, S.r64, EPI_YZ, RED_NORM, h->kappa * h->kappa, S.bhat, 1.0, S.x64, -1.0,
+                             ST_OUTER, GUARD_NONE, s));
+            nk += S.nrhs + 2;
+        } else {
+            WD_CUDA(h, cudaMemsetAsync(S.x64, 0, vec_bytes(h, WD_FP64) * S.nrhs, s));
+            WD_CUDA(h, cudaMemcpyAsync(S.r64, S.bhat, vec_bytes(h, WD_FP64) * S.nrhs, cudaMemcpyDeviceToDevice, s));
+            WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.r64, red_ctx(h, ST_OUTER), GUARD_NONE, s));
+            nk += 1;
+        }
+    }
+    int rc = read_states(sys, s);
+    if (rc != WD_OK) return rc;
+
+    // inner-iteration graph: cached in the handle for single-system calls
+    cudaGraphExec_t exec = nullptr;
+    bool own_exec = false;
+    if (sys.size() == 1) {
+        GraphKey key{prec, recon_lo, scale_pass ? 1 : 0, ips, sys[0].nrhs, h0->gen};
+        auto it = h0->graphs.find(key);
+        if (it != h0->graphs.end()) {
+            exec = it->second;
+        } else {
+            if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, ips, &exec)) != WD_OK) return rc;
+            h0->graphs[key] = exec;
+        }
+    } else {
+        if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, ips, &exec)) != WD_OK) return rc;
+        own_exec = true;
+    }
+    long long graph_kernels = 0;
+    for (size_t i = 0; i < sys.size(); ++i) graph_kernels += (long long)ips * kpi + 1;
+
+    std::vector<int> status(total_rhs, WD_OK);
+    int trips = 0;
+    for (;;) {
+        // decide, per right-hand side, whether to continue (outer stopping rule)
+        bool any = false;
+        int k = 0;
+        for (auto& S : sys) {
+            for (int r = 0; r < S.nrhs; ++r, ++k) {
+                SolverState& q = S.h->hst[r];
+                if (trips == 0) S.eta_norm[r] = std::sqrt(q.acc);
+                const double rn = q.rnorm, en = S.eta_norm[r];
+                out[k].outer_residual = en > 0 ? rn / en : 0.0;
+                bool act = (rn > tol * en) && status[k] == WD_OK;
+                if (act && !std::isfinite(rn)) {
+                    status[k] = WD_ERR_NONFINITE;
+                    act = false;
+                }
+                if (!std::isfinite(rn) && status[k] == WD_OK) status[k] = WD_ERR_NONFINITE;
+                if (act && out[k].outer_iterations >= prm.max_outer) {
+                    status[k] = WD_ERR_NOT_CONVERGED;
+                    act = false;
+                }
+                S.active[r] = act;
+                q.skip = act ? 0 : 1;
+                if (act) {
+                    any = true;
+                    q.s = prm.s;
+                    q.use_shat = prm.use_shat;
+                    q.sigma = prm.sigma;
+                    q.sigma_lambda = prm.sigma_lambda;
+                    q.omega0 = prm.omega0;
+                    q.recalc = prm.recalc_gamma;
+                    q.rescale_x = prm.rescale_x;
+                    q.scale_pass = scale_pass ? 1 : 0;
+                    q.max_matvecs = prm.max_inner;
+                    // FP64 BiCGStab: one inner solve to the outer tolerance; mixed: eps of Table 2
+                    q.eps = cfg.fp64_inner ? std::max(0.5 * tol * en / rn, 1e-15) : prm.inner_eps;
+                    q.done = 0;
+                }
+            }
+        }
+        if ((rc = write_states(sys, s)) != WD_OK) return rc;
+        if (!any) break;
+        // y~ = low_prec((s / |r|) r) ; s^ = |single(y~)| ; inner start
+        for (auto& S : sys) {
+            cudaError_t e = by_prec(prec, [&](auto tag) {
+                typedef typename decltype(tag)::type T;
+                return Ops<T>::rescale_in(S.h->g.Vh, S.nrhs, S.vs, S.vs64, S.r64, S.r, S.rs, prm.ftz, S.h->st,
+                                          red_ctx(S.h, ST_INIT), s);
+            });
+            WD_CUDA(S.h, e);
+            nk += 1;
+        }
+        // inner BiCGStab of all systems: graph launches, activity flag read one launch behind
+        const int max_launch = prm.max_inner / (2 * ips) + 3;
+        for (int kk = 0;; ++kk) {
+            WD_CUDA(h0, cudaGraphLaunch(exec, s));
+            nk += graph_kernels;
+            WD_CUDA(h0, cudaMemcpyAsync(&h0->hflag[kk & 1], h0->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            WD_CUDA(h0, cudaEventRecord(h0->ev[kk & 1], s));
+            if (kk >= 1) {
+                WD_CUDA(h0, cudaEventSynchronize(h0->ev[(kk - 1) & 1]));
+                if (!h0->hflag[(kk - 1) & 1]) break;
+            }
+            if (kk + 1 >= max_launch) break;
+        }
+        // x += (|r| / s^) double(t~) / lambda' ; r = b^ - A x in FP64
+        for (auto& S : sys) {
+            wd_handle* h = S.h;
+            cudaError_t e = by_prec(prec, [&](auto tag) {
+                typedef typename decltype(tag)::type T;
+                return Ops<T>::correct(h->g.Vh, S.nrhs, S.vs, S.vs64, S.x64, S.xt, h->st, s);
+            });
+            WD_CUDA(h, e);
+            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE,
+                             GUARD_OUTER, s));
+            WD_CUDA(h, hop64(S, 0, S.tmp64, S.r64, EPI_YZ, RED_NORM, h->kappa * h->kappa, S.bhat, 1.0, S.x64, -1.0,
+                             ST_OUTER, GUARD_OUTER, s));
+            nk += 3;
+        }
+        if ((rc = read_states(sys, s)) != WD_OK) return rc;
+        ++trips;
+        k = 0;
+        for (auto& S : sys) {
+            for (int r = 0; r < S.nrhs; ++r, ++k) {
+                if (!S.active[r]) continue;
+                const SolverState& q = S.h->hst[r];
+                out[k].outer_iterations += 1;
+                out[k].inner_iterations += q.iter;
+                out[k].inner_matvecs += q.matvecs;
+                out[k].outer_matvecs += 1;
+                if (out[k].outer_iterations == 1) out[k].first_inner_nonzeros = q.nonzeros;
+                if (q.status == S_NONFINITE) status[k] = WD_ERR_NONFINITE;
+            }
+        }
+    }
+    if (own_exec) cudaGraphExecDestroy(exec);
+
+    // Eq. 5: xi_o = eta_o + kappa H_oe xi_e ; true residual |eta - D xi| in FP64
+    for (auto& S : sys)
+        for (int r = 0; r < S.nrhs; ++r) S.h->hst[r].skip = 0;
+    if ((rc = write_states(sys, s)) != WD_OK) return rc;
+    for (auto& S : sys) {
+        wd_handle* h = S.h;
+        const double kap = h->kappa;
+        const size_t len = (size_t)2 * h->g.Vh * 24;
+        WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.eta_o, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE, s));
+        WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.x64, -1.0, ST_ACC_SET,
+                         GUARD_NONE, s));
+        WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.xo, -1.0, ST_ACC, GUARD_NONE,
+                         s));
+        for (int r = 0; r < S.nrhs; ++r) {
+            WD_CUDA(h, Ops<double>::unpack(h->g, 0, S.x64 + r * S.vs64, S.xl + r * len, s));
+            WD_CUDA(h, Ops<double>::unpack(h->g, 1, S.xo + r * S.vs64, S.xl + r * len, s));
+        }
+        if (!S.x_dev) WD_CUDA(h, cudaMemcpyAsync(S.x, S.xl, S.nrhs * len * sizeof(double), cudaMemcpyDeviceToHost, s));
+        nk += 3 + 2 * S.nrhs;
+    }
+    WD_CUDA(h0, cudaEventRecord(h0->t1, s));
+    if ((rc = read_states(sys, s)) != WD_OK) return rc;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h0->t0, h0->t1);
+    int worst = WD_OK;
+    int k = 0;
+    for (auto& S : sys) {
+        for (int r = 0; r < S.nrhs; ++r, ++k) {
+            const double en = S.eta_norm[r];
+            wd_solve_stats& o = out[k];
+            o.elapsed_ms = ms;
+            o.kernel_launches = nk;
+            o.true_residual = en > 0 ? std::sqrt(S.h->hst[r].acc) / en : 0.0;
+            if (o.outer_iterations == 0) o.first_inner_nonzeros = -1;
+            int st = status[k];
+            if (st == WD_OK && !(o.true_residual <= tol))
+                st = std::isfinite(o.true_residual) ? WD_ERR_NOT_CONVERGED : WD_ERR_NONFINITE;
+            o.status = st;
+            if (st != WD_OK && worst == WD_OK) worst = st;
+            if (stats) stats[k] = o;
+        }
+    }
+    if (worst != WD_OK)
+        fail(h0, worst, "solve: %s (first failing right-hand side of %d, %d refinement trips)",
+             wd_status_string(worst), total_rhs, trips);
+    return worst;
 }
 
 }  // namespace wd
@@ -177,192 +503,7 @@ extern "C" int wd_solve_params_default(int scheme, wd_solve_params* p) {
 extern "C" int wd_solve(wd_handle* h, const double* b, double* x, double tol, int scheme,
                         const wd_solve_params* params, wd_solve_stats* stats, void* stream) {
     if (!h) return WD_ERR_INVALID_ARG;
-    SchemeCfg cfg;
-    if (!b || !x || !(tol > 0) || !scheme_cfg(scheme, &cfg)) return fail(h, WD_ERR_INVALID_ARG, "wd_solve: bad argument");
-    wd_solve_params prm;
-    if (params) prm = *params; else wd_solve_params_default(scheme, &prm);
-    if (!valid_recon(prm.recon) || prm.max_outer < 1 || prm.max_inner < 2 || !(prm.s > 0) || prm.sigma < 0 ||
-        prm.iters_per_sync < 1 || (prm.rescale_x && !(prm.sigma_lambda > 0)))
-        return fail(h, WD_ERR_INVALID_ARG, "wd_solve: bad parameters");
-    if (!h->have_gauge) return fail(h, WD_ERR_NO_GAUGE, "wd_set_gauge has not been called");
-    int rc = ensure_solver_state(h);
-    if (rc != WD_OK) return rc;
-    const int prec = cfg.prec;
-    const int recon_lo = cfg.fp64_inner ? 18 : prm.recon;
-    const uint4 *le64, *lo64, *le, *lo;
-    if ((rc = ensure_links(h, WD_FP64, 18, &le64, &lo64)) != WD_OK) return rc;
-    if ((rc = ensure_links(h, prec, recon_lo, &le, &lo)) != WD_OK) return rc;
-
-    cudaStream_t s = (cudaStream_t)stream;
-    const int n = h->g.Vh;
-    const size_t b64 = vec_bytes(h, WD_FP64);
-    const size_t lexb = (size_t)2 * n * 24 * sizeof(double);
-    uint4* eta_e = (uint4*)workspace(h, "f64.eta_e", b64);
-    uint4* eta_o = (uint4*)workspace(h, "f64.eta_o", b64);
-    uint4* bhat = (uint4*)workspace(h, "f64.bhat", b64);
-    uint4* x64 = (uint4*)workspace(h, "f64.x", b64);
-    uint4* r64 = (uint4*)workspace(h, "f64.r", b64);
-    uint4* tmp64 = (uint4*)workspace(h, "f64.tmp", b64);
-    uint4* xo = (uint4*)workspace(h, "f64.xo", b64);
-    if (!eta_e || !eta_o || !bhat || !x64 || !r64 || !tmp64 || !xo) return fail(h, WD_ERR_CUDA, "out of device memory");
-    InnerVecs iv;
-    if (cfg.fp64_inner || prec != WD_FP64) {
-        if ((rc = inner_vecs(h, prec, &iv)) != WD_OK) return rc;
-    }
-
-    const bool b_dev = is_device_ptr(b), x_dev = is_device_ptr(x);
-    double* bl = const_cast<double*>(b);
-    double* xl = x;
-    if (!b_dev || !x_dev) {
-        double* stage = (double*)workspace(h, "lex.stage", lexb);
-        if (!stage) return fail(h, WD_ERR_CUDA, "out of device memory");
-        if (!b_dev) bl = stage;
-        if (!x_dev) xl = stage;   // b is consumed (packed) before x is written
-    }
-
-    WD_CUDA(h, cudaEventRecord(h->t0, s));
-    if (!b_dev) WD_CUDA(h, cudaMemcpyAsync(bl, b, lexb, cudaMemcpyHostToDevice, s));
-    const double kappa = h->kappa;
-    HopParams P{};
-    P.g = h->g;
-    P.rc = red_ctx(h, ST_NONE);
-    P.guard = nullptr;   // FP64 refinement kernels never exit early
-
-    auto hop64 = [&](int parity, const uint4* in, uint4* out, int epi, int red, double a, const uint4* y, double bb,
-                     const uint4* z, double c, int stage) {
-        P.parity = parity;
-        P.links = parity == 0 ? le64 : lo64;
-        P.in = in;
-        P.out = out;
-        P.y = y;
-        P.z = z;
-        P.a = a;
-        P.b = bb;
-        P.c = c;
-        P.rc = red_ctx(h, stage);
-        return Ops<double>::hop(18, epi, red, P, s);
-    };
-
-    long long nk = 0;   // kernels launched by this call
-    // Eq. 4 right-hand side: b^ = eta_e + kappa H_eo eta_o ; |eta|^2
-    nk += 5;
-    WD_CUDA(h, Ops<double>::pack(h->g, 0, bl, eta_e, s));
-    WD_CUDA(h, Ops<double>::pack(h->g, 1, bl, eta_o, s));
-    WD_CUDA(h, Ops<double>::norm2(n, eta_e, red_ctx(h, ST_ACC_SET), s));
-    WD_CUDA(h, Ops<double>::norm2(n, eta_o, red_ctx(h, ST_ACC), s));
-    WD_CUDA(h, hop64(0, eta_o, bhat, EPI_Y, RED_NONE, kappa, eta_e, 1.0, nullptr, 0.0, ST_NONE));
-    // r = b^ - A x
-    nk += prm.x_is_guess ? 3 : 1;
-    if (prm.x_is_guess) {
-        if (!x_dev) WD_CUDA(h, cudaMemcpyAsync(xl, x, lexb, cudaMemcpyHostToDevice, s));
-        WD_CUDA(h, Ops<double>::pack(h->g, 0, xl, x64, s));
-        WD_CUDA(h, hop64(1, x64, tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE));
-        WD_CUDA(h, hop64(0, tmp64, r64, EPI_YZ, RED_NORM, kappa * kappa, bhat, 1.0, x64, -1.0, ST_OUTER));
-    } else {
-        WD_CUDA(h, cudaMemsetAsync(x64, 0, b64, s));
-        WD_CUDA(h, cudaMemcpyAsync(r64, bhat, b64, cudaMemcpyDeviceToDevice, s));
-        WD_CUDA(h, Ops<double>::norm2(n, r64, red_ctx(h, ST_OUTER), s));
-    }
-    if ((rc = read_state(h, s)) != WD_OK) return rc;
-    const double eta_norm = std::sqrt(h->hst->acc);
-
-    wd_solve_stats out{};
-    out.status = WD_OK;
-    out.first_inner_nonzeros = -1;
-    int status = WD_OK;
-    const bool scale_pass = prm.sigma > 0 || prm.rescale_x;
-    const int ips = prm.iters_per_sync;
-    cudaGraphExec_t exec = nullptr;
-    if ((rc = inner_graph(h, prec, recon_lo, scale_pass, ips, iv, le, lo, &exec)) != WD_OK) return rc;
-
-    int trips = 0;
-    for (;;) {
-        const double rn = h->hst->rnorm;
-        out.outer_residual = eta_norm > 0 ? rn / eta_norm : 0.0;
-        if (!(rn > tol * eta_norm)) {
-            if (!std::isfinite(rn)) status = WD_ERR_NONFINITE;
-            break;
-        }
-        if (trips >= prm.max_outer) {
-            status = WD_ERR_NOT_CONVERGED;
-            break;
-        }
-        // configure the inner solve (Alg. 3 / Alg. 4 parameters)
-        SolverState* hs = h->hst;
-        hs->s = prm.s;
-        hs->use_shat = prm.use_shat;
-        hs->sigma = prm.sigma;
-        hs->sigma_lambda = prm.sigma_lambda;
-        hs->omega0 = prm.omega0;
-        hs->recalc = prm.recalc_gamma;
-        hs->rescale_x = prm.rescale_x;
-        hs->scale_pass = scale_pass ? 1 : 0;
-        hs->max_matvecs = prm.max_inner;
-        // FP64 BiCGStab: one inner solve to the outer tolerance; mixed: eps of Table 2
-        hs->eps = cfg.fp64_inner ? std::max(0.5 * tol * eta_norm / rn, 1e-15) : prm.inner_eps;
-        hs->done = 0;
-        if ((rc = write_state(h, s)) != WD_OK) return rc;
-        // y~ = low_prec((s / |r|) r) ; s^ = |single(y~)| ; inner start
-        cudaError_t e = by_prec(prec, [&](auto tag) {
-            typedef typename decltype(tag)::type T;
-            return Ops<T>::rescale_in(n, r64, iv.r, iv.rs, prm.ftz, h->st, red_ctx(h, ST_INIT), s);
-        });
-        WD_CUDA(h, e);
-        // inner BiCGStab: graph launches, done flag read one launch behind
-        const int max_launch = prm.max_inner / (2 * ips) + 3;
-        nk += 4;   // rescale, correction, two FP64 hops
-        for (int k = 0;; ++k) {
-            WD_CUDA(h, cudaGraphLaunch(exec, s));
-            nk += (long long)ips * (scale_pass ? 8 : 7);
-            WD_CUDA(h, cudaMemcpyAsync(&h->hflag[k & 1], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-            WD_CUDA(h, cudaEventRecord(h->ev[k & 1], s));
-            if (k >= 1) {
-                WD_CUDA(h, cudaEventSynchronize(h->ev[(k - 1) & 1]));
-                if (h->hflag[(k - 1) & 1]) break;
-            }
-            if (k + 1 >= max_launch) break;
-        }
-        // x += (|r| / s^) double(t~) / lambda'
-        e = by_prec(prec, [&](auto tag) {
-            typedef typename decltype(tag)::type T;
-            return Ops<T>::correct(n, x64, iv.x, h->st, s);
-        });
-        WD_CUDA(h, e);
-        // r = b^ - A x in FP64
-        WD_CUDA(h, hop64(1, x64, tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE));
-        WD_CUDA(h, hop64(0, tmp64, r64, EPI_YZ, RED_NORM, kappa * kappa, bhat, 1.0, x64, -1.0, ST_OUTER));
-        if ((rc = read_state(h, s)) != WD_OK) return rc;
-        ++trips;
-        out.inner_iterations += h->hst->iter;
-        out.inner_matvecs += h->hst->matvecs;
-        out.outer_matvecs += 1;
-        if (trips == 1) out.first_inner_nonzeros = h->hst->nonzeros;
-        if (h->hst->status == S_NONFINITE) {
-            status = WD_ERR_NONFINITE;
-            break;
-        }
-    }
-
-    // Eq. 5: xi_o = eta_o + kappa H_oe xi_e ; true residual |eta - D xi| in FP64
-    nk += 5;
-    WD_CUDA(h, hop64(1, x64, xo, EPI_Y, RED_NONE, kappa, eta_o, 1.0, nullptr, 0.0, ST_NONE));
-    WD_CUDA(h, hop64(0, xo, r64, EPI_YZ, RED_NORM, kappa, eta_e, 1.0, x64, -1.0, ST_ACC_SET));
-    WD_CUDA(h, hop64(1, x64, tmp64, EPI_YZ, RED_NORM, kappa, eta_o, 1.0, xo, -1.0, ST_ACC));
-    WD_CUDA(h, Ops<double>::unpack(h->g, 0, x64, xl, s));
-    WD_CUDA(h, Ops<double>::unpack(h->g, 1, xo, xl, s));
-    if (!x_dev) WD_CUDA(h, cudaMemcpyAsync(x, xl, lexb, cudaMemcpyDeviceToHost, s));
-    WD_CUDA(h, cudaEventRecord(h->t1, s));
-    if ((rc = read_state(h, s)) != WD_OK) return rc;
-    float ms = 0;
-    cudaEventElapsedTime(&ms, h->t0, h->t1);
-    out.elapsed_ms = ms;
-    out.outer_iterations = trips;
-    out.kernel_launches = nk;
-    out.true_residual = eta_norm > 0 ? std::sqrt(h->hst->acc) / eta_norm : 0.0;
-    if (status == WD_OK && !(out.true_residual <= tol)) status = std::isfinite(out.true_residual) ? WD_ERR_NOT_CONVERGED : WD_ERR_NONFINITE;
-    out.status = status;
-    if (stats) *stats = out;
-    if (status != WD_OK) fail(h, status, "wd_solve: %s (true residual %g, %d trips)", wd_status_string(status),
-                              out.true_residual, trips);
-    return status;
+    if (!b || !x) return fail(h, WD_ERR_INVALID_ARG, "wd_solve: null source or solution");
+    const int one = 1;
+    return solve_systems(1, &h, &one, &b, &x, tol, scheme, params, stats, (cudaStream_t)stream);
 }

@@ -162,6 +162,10 @@ class Lattice:
         self._check(lib().wd_apply(self.h, PREC.get(prec, prec), recon, op, _ptr(x), _ptr(y), _stream(stream)),
                     "wd_apply")
 
+    def solve_rhs(self, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):
+        """Several right-hand sides of this lattice in one batched solve; b, x: [nrhs, ...] float64."""
+        return solve_batch([self], [b], [x], tol, scheme, params, stream, check)
+
     def solve(self, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):
         """Solve D_W x = b; b, x float64 full-lattice tensors (host layout), CPU or CUDA."""
         sc = SCHEME.get(scheme, scheme)
@@ -171,3 +175,23 @@ class Lattice:
         if check:
             self._check(rc, "wd_solve")
         return st
+
+
+def solve_batch(lattices, bs, xs, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):
+    """wd_solve_batch: lattice i solves bs[i] ([nrhs_i, ...] float64, device) into xs[i].
+
+    Returns the list of per-right-hand-side SolveStats (lattice-major order).
+    """
+    n = len(lattices)
+    sc = SCHEME.get(scheme, scheme)
+    prm = params if params is not None else default_params(sc)
+    nr = [int(b.shape[0]) for b in bs]
+    hs = (C.c_void_p * n)(*[lat.h for lat in lattices])
+    nrhs = (C.c_int * n)(*nr)
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    stats = (SolveStats * max(1, sum(nr)))()
+    rc = lib().wd_solve_batch(n, hs, nrhs, bp, xp, float(tol), sc, C.byref(prm), stats, _stream(stream))
+    if check and rc != WD_OK:
+        raise WDError(rc, f"wd_solve_batch: {lib().wd_last_error(lattices[0].h).decode()}")
+    return list(stats)[:sum(nr)]
