@@ -89,7 +89,9 @@ enum wd_scheme {
     WD_MIXED_FP32 = 1,        /* Alg. 1 refinement, FP32 inner BiCGStab without rescaling */
     WD_MIXED_FP16_PLAIN = 2,  /* Alg. 1 refinement, FP16 inner without rescaling          */
     WD_MIXED_FP16 = 3,        /* Alg. 2 refinement, FP16 inner Alg. 3 / Alg. 4            */
-    WD_MIXED_BF16 = 4         /* as WD_MIXED_FP16 with BF16 storage (Sec. 6 outlook)      */
+    WD_MIXED_BF16 = 4,        /* as WD_MIXED_FP16 with BF16 storage (Sec. 6 outlook)      */
+    WD_MIXED_FP16_LEARNED = 5 /* as WD_MIXED_FP16, inner BiCGStab on A M with the learned
+                                 right preconditioner M (wd_precond_set first)            */
 };
 
 /* Knobs of Algorithms 1-4. wd_solve_params_default() fills the values a
@@ -182,6 +184,44 @@ int wd_solve(wd_handle* h, const double* b, double* x, double tol, int scheme,
 int wd_solve_batch(int n, wd_handle* const* h, const int* nrhs, const double* const* b,
                    double* const* x, double tol, int scheme, const wd_solve_params* params,
                    wd_solve_stats* per_rhs_stats, void* stream);
+
+/* ---- Learned right preconditioner M --------------------------------------
+ * A linear, gauge-equivariant parallel-transport network with channels
+ * 1 -> 12 -> 1 (not in the paper; its inner solve is the paper's Alg. 3 on
+ * A M). One layer maps C_in to C_out quark-field channels:
+ *   out[c](x) = sum_{k=0..8} sum_{c'} W[k][c][c'] (T_k in[c'])(x),
+ * hop k = 0 is the identity; k = 1 + d for d = 2 mu transports from x + mu with
+ * U_mu(x), and for d = 2 mu + 1 from x - mu with U_mu(x - mu)^+, with the
+ * boundary phases of the Wilson matrix; W[k][c][c'] is a complex 4x4 spin
+ * matrix. M maps even-site vectors to even-site vectors.
+ * Weight layout (WD_PRECOND_FLOATS floats): layer 1 W1[k][c][s][t][re,im]
+ * (c = hidden channel), then layer 2 W2[k][c][s][t][re,im]. The kernels use
+ * the BF16-rounded weights with FP32 arithmetic. */
+#define WD_PRECOND_FLOATS 6912
+
+/* Load FP32 master weights (host or device memory); resets the Adam state. */
+int wd_precond_set(wd_handle* h, const float* w, int where);
+
+/* Copy the FP32 master weights out (host or device memory). */
+int wd_precond_get(wd_handle* h, float* w, int where);
+
+/* out = M in for packed even-site vectors in precision WD_FP32 (FP32 hidden
+ * channels, FP32 18-real links) or WD_FP16 (BF16 hidden channels, FP16 12-real
+ * links, as inside the WD_MIXED_FP16_LEARNED solve). */
+int wd_precond_apply(wd_handle* h, int prec, const void* in, void* out, void* stream);
+
+/* Training loss L = sum_i |M v_i - y_i|^2 / |y_i|^2 + mu |A M v_i - v_i|^2 / |v_i|^2
+ * over n samples (v_i, y_i = A^{-1} v_i): packed FP32 even-site vectors stored
+ * back to back in device memory. Writes L to *loss and, if grad is not NULL,
+ * dL/dRe W + i dL/dIm W (flat weight layout, device memory) to grad.
+ * Synchronizes `stream`. */
+int wd_precond_grad(wd_handle* h, int n, const float* v, const float* y, double mu, float* grad, double* loss,
+                    void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999) with learning rate lr on the loss of
+ * wd_precond_grad; *loss receives the loss before the step. */
+int wd_precond_train_step(wd_handle* h, int n, const float* v, const float* y, double mu, double lr, double* loss,
+                          void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* wd_status_string(int status);

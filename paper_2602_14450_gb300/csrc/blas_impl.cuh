@@ -82,21 +82,25 @@ __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, 
 // sums: |r|^2, |x|^2, (r*, r) [the last only when WITH_RS]
 template <typename T, bool WITH_RS>
 __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
-                                            const uint4* t, const uint4* rstar, SolverState* sts, RedCtx rc) {
+                                            const uint4* t, const uint4* rstar, const uint4* xr_src,
+                                            const uint4* xp_src, SolverState* sts, RedCtx rc) {
     typedef typename Unit<T>::C C;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
     if (guarded(st, GUARD_INNER)) return;
     const long long o = sl.rhs * vs;
     x += o; r += o; p += o; t += o; rstar += o;
+    // x-update sources: r and p, or M r and M p with a right preconditioner
+    const uint4* xsr = xr_src ? xr_src + o : r;
+    const uint4* xsp = xp_src ? xp_src + o : p;
     const bool first = st->first;
     const C xr_r = (C)st->cXr[0], xr_i = (C)st->cXr[1], xp_r = (C)st->cXp[0], xp_i = (C)st->cXp[1];
     const C om_r = (C)-st->omega[0], om_i = (C)-st->omega[1];
     C s_r2 = 0, s_x2 = 0, s_re = 0, s_im = 0;
     RHS_LOOP(h, n) {
         C rr[24], pp[24], xx[24], tt[24];
-        load_spinor<T>(r, n, h, rr);
-        load_spinor<T>(p, n, h, pp);
+        load_spinor<T>(xsr, n, h, rr);
+        load_spinor<T>(xsp, n, h, pp);
         if (first) {
 #pragma unroll
             for (int i = 0; i < 24; ++i) xx[i] = 0;
@@ -109,6 +113,7 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
             cscale_add(xx[2 * i], xx[2 * i + 1], xp_r, xp_i, pp[2 * i], pp[2 * i + 1]);
         }
         store_spinor<T>(x, n, h, xx);
+        if (xr_src) load_spinor<T>(r, n, h, rr);
         load_spinor<T>(t, n, h, tt);
 #pragma unroll
         for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, tt[2 * i], tt[2 * i + 1]);

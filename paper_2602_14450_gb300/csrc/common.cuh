@@ -155,6 +155,42 @@ __device__ __forceinline__ int lex_of(const Geom& g, int p, int h) {
     return x + g.L[0] * row;
 }
 
+// Coordinates of site h on parity p.
+struct Coord {
+    int x, y, z, t, row;
+};
+__device__ __forceinline__ Coord coord_of(const Geom& g, int p, int h) {
+    Coord c;
+    c.row = h / g.Lxh;
+    const int xh = h - c.row * g.Lxh;
+    c.y = c.row % g.L[1];
+    const int r2 = c.row / g.L[1];
+    c.z = r2 % g.L[2];
+    c.t = r2 / g.L[2];
+    c.x = 2 * xh + ((p + c.y + c.z + c.t) & 1);
+    return c;
+}
+
+// Site index (on the other parity) of the neighbour of site h in direction
+// d = 2 mu (+mu) or 2 mu + 1 (-mu); *wrap says whether the hop wraps.
+__device__ __forceinline__ int neighbour(const Geom& g, int h, const Coord& c, int d, bool* wrap) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int Lxh = g.Lxh;
+    if (mu == 0) {
+        const bool w = fwd ? (c.x == g.L[0] - 1) : (c.x == 0);
+        *wrap = w;
+        const int xn = fwd ? (w ? 0 : c.x + 1) : (w ? g.L[0] - 1 : c.x - 1);
+        return c.row * Lxh + (xn >> 1);
+    }
+    const int coordv = mu == 1 ? c.y : mu == 2 ? c.z : c.t;
+    const int L = g.L[mu];
+    const int s = mu == 1 ? Lxh : mu == 2 ? Lxh * g.L[1] : Lxh * g.L[1] * g.L[2];
+    const bool w = fwd ? (coordv == L - 1) : (coordv == 0);
+    *wrap = w;
+    return fwd ? (w ? h - (L - 1) * s : h + s) : (w ? h + (L - 1) * s : h - s);
+}
+
 // ---------------------------------------------------------------- complex ---
 
 template <typename C> struct cpx {

@@ -52,6 +52,9 @@ struct wd_handle {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+
+    bool have_precond = false;         // weights of the learned preconditioner loaded
+    long long adam_t = 0;              // Adam steps taken on those weights
 };
 
 namespace wd {

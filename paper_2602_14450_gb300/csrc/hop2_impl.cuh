@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
                 part[0] += re.x + re.y;
                 part[1] += im.x + im.y;
             }
-        } else if constexpr (RED == RED_TS) {          // (o, y), (o, o), (y, y)
+        } else if constexpr (RED == RED_TS) {          // (o, q), (o, o), (q, q); q = rstar if given, else y
+            if (vrs) load_pair<T>(vrs, Vh, ha, hb, yv);
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
                 const float2 yr = mul2(yv[2 * i], SC2), yi = mul2(yv[2 * i + 1], SC2);

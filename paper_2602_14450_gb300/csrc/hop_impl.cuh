@@ -244,13 +244,20 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
                 part[0] += rs[2 * i] * o[2 * i] + rs[2 * i + 1] * o[2 * i + 1];
                 part[1] += rs[2 * i] * o[2 * i + 1] - rs[2 * i + 1] * o[2 * i];
             }
-        } else if constexpr (RED == RED_TS) {          // (o, y), (o, o), (y, y)
+        } else if constexpr (RED == RED_TS) {          // (o, q), (o, o), (q, q); q = rstar if given, else y
+            C qv[24];
+            if (vrs) {
+                load_spinor<T>(vrs, Vh, h, qv);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 24; ++i) qv[i] = yv[i];
+            }
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
-                part[0] += o[2 * i] * yv[2 * i] + o[2 * i + 1] * yv[2 * i + 1];
-                part[1] += o[2 * i] * yv[2 * i + 1] - o[2 * i + 1] * yv[2 * i];
+                part[0] += o[2 * i] * qv[2 * i] + o[2 * i + 1] * qv[2 * i + 1];
+                part[1] += o[2 * i] * qv[2 * i + 1] - o[2 * i + 1] * qv[2 * i];
                 part[2] += o[2 * i] * o[2 * i] + o[2 * i + 1] * o[2 * i + 1];
-                part[NS - 1] += yv[2 * i] * yv[2 * i] + yv[2 * i + 1] * yv[2 * i + 1];
+                part[NS - 1] += qv[2 * i] * qv[2 * i] + qv[2 * i + 1] * qv[2 * i + 1];
             }
         } else if constexpr (RED == RED_NORM) {
 #pragma unroll

@@ -51,7 +51,8 @@ template <typename T> struct Ops {
     static cudaError_t supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
                                cudaStream_t s);
     static cudaError_t xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
-                          const uint4* t, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s);
+                          const uint4* t, const uint4* rstar, const uint4* xr_src, const uint4* xp_src,
+                          SolverState* st, RedCtx rc, cudaStream_t s);
     static cudaError_t scale(int n, int nrhs, long long vs, uint4* r, uint4* x, const uint4* rstar, SolverState* st,
                              RedCtx rc, cudaStream_t s);
     static cudaError_t rescale_in(int n, int nrhs, long long vs, long long vs64, const uint4* r64, uint4* r,

@@ -97,13 +97,14 @@ cudaError_t Ops<T>::supdate(int n, int nrhs, long long vs, uint4* r, const uint4
 
 template <typename T>
 cudaError_t Ops<T>::xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
-                       const uint4* t, const uint4* rstar, SolverState* st, RedCtx rc, cudaStream_t s) {
+                       const uint4* t, const uint4* rstar, const uint4* xr_src, const uint4* xp_src,
+                       SolverState* st, RedCtx rc, cudaStream_t s) {
     if (with_rs) {
         const int nb = reduce_blocks((const void*)k_xr<T, true>, n, VEC_BLOCK, nrhs);
-        k_xr<T, true><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, st, rc);
+        k_xr<T, true><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);
     } else {
         const int nb = reduce_blocks((const void*)k_xr<T, false>, n, VEC_BLOCK, nrhs);
-        k_xr<T, false><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, st, rc);
+        k_xr<T, false><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,552 @@
+// Learned right preconditioner M: a linear, gauge-equivariant parallel-transport
+// convolution network with channels 1 -> 12 -> 1 (SURVEY a13/a14 form).
+//
+//   layer: out[c](x) = sum_{k=0..8} sum_{c'} W[k, c, c'] (T_k in[c'])(x)
+//   T_0 = 1, T_{1+d} with d = 2 mu: U_mu(x) f(x+mu); d = 2 mu + 1: U_mu(x-mu)^+ f(x-mu)
+//
+// The transport of site x in direction d uses exactly the gathered link d of
+// the hop kernels (hop_impl.cuh) and the same boundary phases. W[k, c, c'] is
+// a complex 4x4 matrix on spin. M maps an even-site vector to an even-site
+// vector: layer 1 fans the single input channel out to 12 hidden channels on
+// all sites, layer 2 folds them back onto the even sites.
+//
+// Weights (flat float layout shared with the C ABI): W1[k][c][s][t][re,im]
+// then W2[k][c][s][t][re,im], 9 * 12 * 16 complex each. The kernels read them
+// as given (the library stores BF16-rounded values for the solver).
+//
+// Training kernels compute, for L = sum |M v - y|^2/|y|^2 + mu |A M v - v|^2/|v|^2,
+// the weight gradients dL/dRe W + i dL/dIm W by the adjoint network.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "blas_impl.cuh"
+#include "handle.h"
+
+namespace wd {
+
+constexpr int PTC_C = 12;                 // hidden channels
+constexpr int PTC_LAYER = 9 * PTC_C * 16; // complex weights per layer
+constexpr int PTC_FLOATS = 2 * PTC_LAYER * 2;
+
+// Link d of site h (gathered layout, R reals of LT) as 18 floats (row 2 rebuilt for R = 12).
+template <typename LT, int R>
+__device__ __forceinline__ void load_link(const uint4* __restrict__ links, int Vh, int h, int d, float (&m)[18]) {
+    constexpr int N = Unit<LT>::N;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const int el = d * R + e;
+        const uint4 w = __ldg(links + (size_t)(el / N) * Vh + h);
+        m[e] = (float)Unit<LT>::get(w, el % N);
+    }
+    if (R == 12) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+            const float ar = m[2 * b1], ai = m[2 * b1 + 1], br = m[6 + 2 * b2], bi = m[6 + 2 * b2 + 1];
+            const float cr = m[2 * b2], ci = m[2 * b2 + 1], dr = m[6 + 2 * b1], di = m[6 + 2 * b1 + 1];
+            m[12 + 2 * b] = ar * br - ai * bi - cr * dr + ci * di;
+            m[12 + 2 * b + 1] = -(ar * bi + ai * br - cr * di - ci * dr);
+        }
+    }
+}
+
+// phi = m f on colour for each of the 4 spins (f, phi: [spin][colour][re,im]).
+__device__ __forceinline__ void colour_mul(const float (&m)[18], const float (&f)[24], float (&phi)[24]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float mr = m[2 * (3 * a + b)], mi = m[2 * (3 * a + b) + 1];
+                const float fr = f[2 * (3 * s + b)], fi = f[2 * (3 * s + b) + 1];
+                re += mr * fr - mi * fi;
+                im += mr * fi + mi * fr;
+            }
+            phi[2 * (3 * s + a)] = re;
+            phi[2 * (3 * s + a) + 1] = im;
+        }
+}
+
+// acc += w phi on spin (w: 16 complex [s][t] as float2 in shared memory).
+__device__ __forceinline__ void spin_mul_add(const float2* w, const float (&phi)[24], float (&acc)[24]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 c = w[4 * s + t];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float fr = phi[2 * (3 * t + a)], fi = phi[2 * (3 * t + a) + 1];
+                acc[2 * (3 * s + a)] += c.x * fr - c.y * fi;
+                acc[2 * (3 * s + a) + 1] += c.x * fi + c.y * fr;
+            }
+        }
+}
+
+// T_k f at site h of parity p, f read from the parity its support lives on.
+// Returns false when that source parity holds no data.
+template <typename TF, typename LT, int R>
+__device__ __forceinline__ bool transported(const Geom& g, int p, int h, const Coord& c, int k, const uint4* f_same,
+                                            const uint4* f_other, const uint4* links_p, float (&phi)[24]) {
+    if (k == 0) {
+        if (!f_same) return false;
+        load_spinor<TF>(f_same, g.Vh, h, phi);
+        return true;
+    }
+    if (!f_other) return false;
+    const int d = k - 1;
+    bool wrap;
+    const int hn = neighbour(g, h, c, d, &wrap);
+    float f[24], m[18];
+    load_spinor<TF>(f_other, g.Vh, hn, f);
+    if (wrap && g.bc[d >> 1] < 0) {
+#pragma unroll
+        for (int i = 0; i < 24; ++i) f[i] = -f[i];
+    }
+    load_link<LT, R>(links_p, g.Vh, h, d, m);
+    colour_mul(m, f, phi);
+    return true;
+}
+
+__device__ __forceinline__ const uint4* H_channel(const uint4* H, long long hvs, int c, int p) {
+    return H + (size_t)(2 * c + p) * hvs;
+}
+
+// Fan-out layer: one input channel (per-parity pointers, null = zero) to
+// channel blockIdx.y of H on parity blockIdx.z. H layout: [c][parity][units][Vh].
+template <typename TIN, typename TH, typename LT, int R>
+__global__ void __launch_bounds__(128) k_ptc_fanout(Geom g, const uint4* in_e, const uint4* in_o, uint4* H,
+                                                    long long hvs, const uint4* links_e, const uint4* links_o,
+                                                    const float* w, const SolverState* guard) {
+    if (guarded(guard, GUARD_INNER)) return;
+    __shared__ float2 ws[9 * 16];
+    const int c = blockIdx.y, p = blockIdx.z;
+    for (int i = threadIdx.x; i < 9 * 16; i += blockDim.x) {
+        const int k = i / 16, e = i % 16;
+        ws[i] = make_float2(w[2 * ((k * PTC_C + c) * 16 + e)], w[2 * ((k * PTC_C + c) * 16 + e) + 1]);
+    }
+    __syncthreads();
+    const uint4* same = p == 0 ? in_e : in_o;
+    const uint4* other = p == 0 ? in_o : in_e;
+    const uint4* links = p == 0 ? links_e : links_o;
+    uint4* out = H + (size_t)(2 * c + p) * hvs;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+        const Coord co = coord_of(g, p, h);
+        float acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < 9; ++k) {
+            float phi[24];
+            if (transported<TIN, LT, R>(g, p, h, co, k, same, other, links, phi)) spin_mul_add(&ws[16 * k], phi, acc);
+        }
+        store_spinor<TH>(out, g.Vh, h, acc);
+    }
+}
+
+// Fan-in layer: the 12 channels of H to one output channel on the even sites.
+template <typename TH, typename TOUT, typename LT, int R>
+__global__ void __launch_bounds__(128) k_ptc_fanin(Geom g, const uint4* H, long long hvs, uint4* out_e,
+                                                   const uint4* links_e, const float* w, const SolverState* guard) {
+    if (guarded(guard, GUARD_INNER)) return;
+    __shared__ float2 ws[9 * PTC_C * 16];
+    for (int i = threadIdx.x; i < 9 * PTC_C * 16; i += blockDim.x) ws[i] = make_float2(w[2 * i], w[2 * i + 1]);
+    __syncthreads();
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+        const Coord co = coord_of(g, 0, h);
+        float acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < 9; ++k) {
+            float m[18];
+            int hn = h;
+            bool wrap = false;
+            if (k > 0) {
+                hn = neighbour(g, h, co, k - 1, &wrap);
+                load_link<LT, R>(links_e, g.Vh, h, k - 1, m);
+            }
+            const float ph = (wrap && g.bc[(k - 1) >> 1] < 0) ? -1.f : 1.f;
+#pragma unroll 1
+            for (int c = 0; c < PTC_C; ++c) {
+                const uint4* src = H + (size_t)(2 * c + (k == 0 ? 0 : 1)) * hvs;
+                float f[24], phi[24];
+                load_spinor<TH>(src, g.Vh, hn, f);
+                if (k == 0) {
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) phi[i] = f[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) f[i] *= ph;
+                    colour_mul(m, f, phi);
+                }
+                spin_mul_add(&ws[16 * (k * PTC_C + c)], phi, acc);
+            }
+        }
+        store_spinor<TOUT>(out_e, g.Vh, h, acc);
+    }
+}
+
+// Weight gradient: dW[k][c] += sum_x sum_colour G_c(x) (x) conj(T_k F_c(x)), summed into
+// grad (float, [k][c][s][t][re,im]). Mode 0 (layer 2): G = one even channel,
+// F = the channels of H. Mode 1 (layer 1): G = the channels of H-shaped g_H,
+// F = one even channel. One block row per (k, c) = (blockIdx.y, blockIdx.z).
+template <typename LT, int R>
+__global__ void __launch_bounds__(128) k_ptc_wgrad(Geom g, int mode, const uint4* G, const uint4* F, long long hvs,
+                                                   const uint4* links_e, const uint4* links_o, float* grad) {
+    const int k = blockIdx.y, c = blockIdx.z;
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    for (int p = 0; p < 2; ++p) {
+        if (mode == 0 && p == 1) break;      // layer-2 output lives on even sites only
+        const uint4* links = p == 0 ? links_e : links_o;
+        const uint4* gsrc = mode == 0 ? G : G + (size_t)(2 * c + p) * hvs;
+        const uint4 *f_same, *f_other;
+        if (mode == 0) {
+            f_same = H_channel(F, hvs, c, p);
+            f_other = H_channel(F, hvs, c, 1 - p);
+        } else {
+            f_same = p == 0 ? F : nullptr;
+            f_other = p == 0 ? nullptr : F;
+        }
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+            const Coord co = coord_of(g, p, h);
+            float phi[24];
+            if (!transported<float, LT, R>(g, p, h, co, k, f_same, f_other, links, phi)) continue;
+            float gv[24];
+            load_spinor<float>(gsrc, g.Vh, h, gv);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {   // g_{s,a} conj(phi_{t,a})
+                        const float gr = gv[2 * (3 * s + a)], gi = gv[2 * (3 * s + a) + 1];
+                        const float fr = phi[2 * (3 * t + a)], fi = phi[2 * (3 * t + a) + 1];
+                        acc[2 * (4 * s + t)] += gr * fr + gi * fi;
+                        acc[2 * (4 * s + t) + 1] += gi * fr - gr * fi;
+                    }
+        }
+    }
+    // block sum of the 32 accumulators, then one atomic add per value
+    __shared__ float sh[32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float v = acc[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+        atomicAdd(grad + 2 * ((k * PTC_C + c) * 16) + threadIdx.x, v);
+    }
+}
+
+}  // namespace wd
+
+namespace wd {
+
+// ------------------------------------------------------------ small kernels ---
+
+// z = a x + b y over n floats (y may be null)
+__global__ void k_f32_lincomb(long long n, float a, const float* x, float b, const float* y, float* z) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[i] = a * x[i] + (y ? b * y[i] : 0.f);
+}
+
+// out += sum x_i y_i (double accumulation, one atomic per block)
+__global__ void k_f32_dot(long long n, const float* x, const float* y, double* out) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += (double)x[i] * (double)y[i];
+    double v[1] = {s};
+    block_sum<1>(v);
+    if (threadIdx.x == 0) atomicAdd(out, v[0]);
+}
+
+// gamma5 of the Dirac representation: (g5 f)_s = -f_{s xor 2}
+__global__ void k_gamma5_f32(int Vh, const uint4* in, uint4* out) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        float f[24], o[24];
+        load_spinor_cg<float>(in, Vh, h, f);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int j = 0; j < 6; ++j) o[6 * s + j] = -f[6 * (s ^ 2) + j];
+        store_spinor<float>(out, Vh, h, o);
+    }
+}
+
+// Fan-out weights of the adjoint of layer 2: Wa[k'][c] = W2[k][c]^+, k' the opposite hop of k.
+__global__ void k_ptc_adjoint_weights(const float* w2, float* wa) {
+    for (int i = threadIdx.x; i < PTC_LAYER; i += blockDim.x) {
+        const int k = i / (PTC_C * 16), c = (i / 16) % PTC_C, s = (i / 4) % 4, t = i % 4;
+        const int ka = k == 0 ? 0 : 1 + ((k - 1) ^ 1);
+        const int src = (k * PTC_C + c) * 16 + 4 * t + s;   // transpose
+        const int dst = (ka * PTC_C + c) * 16 + 4 * s + t;
+        wa[2 * dst] = w2[2 * src];
+        wa[2 * dst + 1] = -w2[2 * src + 1];                 // conjugate
+    }
+}
+
+// Adam on the master weights, then the BF16-rounded copy used by the kernels.
+__global__ void k_adam(int n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                       float c1, float c2, float* weff) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        m[i] = b1 * m[i] + (1.f - b1) * gi;
+        v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
+        w[i] -= lr * (m[i] / c1) / (sqrtf(v[i] / c2) + eps);
+        weff[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+    }
+}
+
+__global__ void k_round_bf16(int n, const float* w, float* weff) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        weff[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+}
+
+// ------------------------------------------------------------------- host ---
+
+static int grid_for(int n, int block) {
+    int g = (n + block - 1) / block;
+    const int cap = num_sms() * 8;
+    return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+struct PtcBufs {
+    float *w, *weff, *m, *v, *grad, *wadj;
+};
+
+static int ptc_bufs(wd_handle* h, PtcBufs* b) {
+    const size_t nb = sizeof(float) * PTC_FLOATS;
+    b->w = (float*)workspace(h, "ptc.w", nb);
+    b->weff = (float*)workspace(h, "ptc.weff", nb);
+    b->m = (float*)workspace(h, "ptc.m", nb);
+    b->v = (float*)workspace(h, "ptc.v", nb);
+    b->grad = (float*)workspace(h, "ptc.grad", nb);
+    b->wadj = (float*)workspace(h, "ptc.wadj", nb / 2);
+    if (!b->w || !b->weff || !b->m || !b->v || !b->grad || !b->wadj) return fail(h, WD_ERR_CUDA, "out of device memory");
+    return WD_OK;
+}
+
+// Hidden buffer of 12 channels x 2 parities in storage type of `prec`.
+static uint4* ptc_hidden(wd_handle* h, int prec, const char* name) {
+    return (uint4*)workspace(h, name, vec_bytes(h, prec) * 2 * PTC_C);
+}
+
+// M in = out: FP32 path (FP32 hidden, FP32 18-real links) or FP16 path
+// (BF16 hidden, FP16 12-real links), weights from `w` (device, flat layout).
+cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* H, const float* w,
+                          const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard) {
+    const Geom& g = h->g;
+    const int blk = 128, gx = grid_for(g.Vh, blk);
+    if (prec == WD_FP32) {
+        const long long hvs = (long long)spinor_units(WD_FP32) * g.Vh;
+        k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), blk, 0, s>>>(g, in_e, nullptr, H, hvs, le, lo, w, guard);
+        k_ptc_fanin<float, float, float, 18><<<gx, blk, 0, s>>>(g, H, hvs, out_e, le, w + 2 * PTC_LAYER, guard);
+    } else {
+        const long long hvs = (long long)spinor_units(WD_BF16) * g.Vh;
+        k_ptc_fanout<__half, __nv_bfloat16, __half, 12><<<dim3(gx, PTC_C, 2), blk, 0, s>>>(g, in_e, nullptr, H, hvs,
+                                                                                         le, lo, w, guard);
+        k_ptc_fanin<__nv_bfloat16, __half, __half, 12><<<gx, blk, 0, s>>>(g, H, hvs, out_e, le, w + 2 * PTC_LAYER, guard);
+    }
+    return cudaGetLastError();
+}
+
+// FP32 even-odd operator A (or A^+ = g5 A g5) on FP32 18-real links.
+static cudaError_t apply_A_f32(wd_handle* h, const uint4* in, uint4* out, uint4* tmp, const uint4* le, const uint4* lo,
+                               cudaStream_t s) {
+    HopParams P{};
+    P.g = h->g;
+    P.nrhs = 1;
+    P.parity = 1;
+    P.links = lo;
+    P.in = in;
+    P.out = tmp;
+    P.a = 1.0;
+    cudaError_t e = Ops<float>::hop(18, EPI_H, RED_NONE, P, s);
+    if (e != cudaSuccess) return e;
+    P.parity = 0;
+    P.links = le;
+    P.in = tmp;
+    P.out = out;
+    P.y = in;
+    P.a = -h->kappa * h->kappa;
+    P.b = 1.0;
+    return Ops<float>::hop(18, EPI_Y, RED_NONE, P, s);
+}
+
+int ptc_grad(wd_handle* h, int n, const float* v, const float* y, double mu, double* loss, cudaStream_t s) {
+    PtcBufs B;
+    int rc = ptc_bufs(h, &B);
+    if (rc != WD_OK) return rc;
+    const uint4 *le, *lo;
+    if ((rc = ensure_links(h, WD_FP32, 18, &le, &lo)) != WD_OK) return rc;
+    const Geom& g = h->g;
+    const size_t vb = vec_bytes(h, WD_FP32);
+    const long long nf = (long long)g.Vh * 24;
+    const long long hvs = (long long)spinor_units(WD_FP32) * g.Vh;
+    uint4* H = ptc_hidden(h, WD_FP32, "ptc.h32");
+    uint4* GH = ptc_hidden(h, WD_FP32, "ptc.gh32");
+    float* m = (float*)workspace(h, "ptc.vm", vb);
+    float* e1 = (float*)workspace(h, "ptc.ve1", vb);
+    float* am = (float*)workspace(h, "ptc.vam", vb);
+    float* t1 = (float*)workspace(h, "ptc.vt1", vb);
+    float* t2 = (float*)workspace(h, "ptc.vt2", vb);
+    float* gv = (float*)workspace(h, "ptc.vg", vb);
+    double* dots = (double*)workspace(h, "ptc.dots", sizeof(double) * (4 * n + 4));
+    if (!H || !GH || !m || !e1 || !am || !t1 || !t2 || !gv || !dots) return fail(h, WD_ERR_CUDA, "out of device memory");
+    const int blk = 256, gv1 = grid_for((int)std::min<long long>(nf, 1LL << 30), blk);
+    WD_CUDA(h, cudaMemsetAsync(dots, 0, sizeof(double) * (4 * n + 4), s));
+    WD_CUDA(h, cudaMemsetAsync(B.grad, 0, sizeof(float) * PTC_FLOATS, s));
+    // input norms first: the gradient coefficients need them
+    for (int i = 0; i < n; ++i) {
+        const float* vi = v + i * nf;
+        const float* yi = y + i * nf;
+        k_f32_dot<<<gv1, blk, 0, s>>>(nf, vi, vi, dots + 4 * i);
+        k_f32_dot<<<gv1, blk, 0, s>>>(nf, yi, yi, dots + 4 * i + 1);
+    }
+    std::vector<double> hd(4 * n + 4);
+    WD_CUDA(h, cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (4 * n + 4), cudaMemcpyDeviceToHost, s));
+    WD_CUDA(h, cudaStreamSynchronize(s));
+    const int gx = grid_for(g.Vh, 128);
+    const dim3 wgrid(std::max(1, num_sms() / 8), 9, PTC_C);
+    k_ptc_adjoint_weights<<<1, 256, 0, s>>>(B.weff + 2 * PTC_LAYER, B.wadj);
+    for (int i = 0; i < n; ++i) {
+        const float* vi = v + i * nf;
+        const float* yi = y + i * nf;
+        const double nv = hd[4 * i], ny = hd[4 * i + 1];
+        // forward: m = M v (hidden H kept for the weight gradient of layer 2)
+        WD_CUDA(h, ptc_apply_raw(h, WD_FP32, (const uint4*)vi, (uint4*)m, H, B.weff, le, lo, s, nullptr));
+        // e1 = m - y ; e2 = A m - v ; A^+ e2 = g5 A g5 e2
+        k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, 1.f, m, -1.f, yi, e1);
+        WD_CUDA(h, apply_A_f32(h, (const uint4*)m, (uint4*)am, (uint4*)t1, le, lo, s));
+        k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, 1.f, am, -1.f, vi, am);
+        k_f32_dot<<<gv1, blk, 0, s>>>(nf, e1, e1, dots + 4 * i + 2);
+        k_f32_dot<<<gv1, blk, 0, s>>>(nf, am, am, dots + 4 * i + 3);
+        k_gamma5_f32<<<gx, 128, 0, s>>>(g.Vh, (const uint4*)am, (uint4*)t2);
+        WD_CUDA(h, apply_A_f32(h, (const uint4*)t2, (uint4*)gv, (uint4*)t1, le, lo, s));
+        k_gamma5_f32<<<gx, 128, 0, s>>>(g.Vh, (const uint4*)gv, (uint4*)t2);
+        // g = 2 e1 / |y|^2 + 2 mu A^+ e2 / |v|^2  (= 2 dL/dconj(m))
+        k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, (float)(2.0 / ny), e1, (float)(2.0 * mu / nv), t2, gv);
+        // layer 2: dW2 += sum g (x) conj(T_k H_c) ; g_H = adjoint network of layer 2 applied to g
+        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 0, (const uint4*)gv, H, hvs, le, lo, B.grad + 2 * PTC_LAYER);
+        k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), 128, 0, s>>>(g, (const uint4*)gv, nullptr, GH, hvs,
+                                                                               le, lo, B.wadj, nullptr);
+        // layer 1: dW1 += sum g_H,c (x) conj(T_k v)
+        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 1, GH, (const uint4*)vi, hvs, le, lo, B.grad);
+        WD_CUDA(h, cudaGetLastError());
+    }
+    WD_CUDA(h, cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (4 * n + 4), cudaMemcpyDeviceToHost, s));
+    WD_CUDA(h, cudaStreamSynchronize(s));
+    double L = 0.0;
+    for (int i = 0; i < n; ++i) L += hd[4 * i + 2] / hd[4 * i + 1] + mu * hd[4 * i + 3] / hd[4 * i];
+    if (loss) *loss = L;
+    return WD_OK;
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+extern "C" int wd_precond_set(wd_handle* h, const float* w, int where) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!w || (where != WD_HOST && where != WD_DEVICE)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_set: bad argument");
+    PtcBufs B;
+    int rc = ptc_bufs(h, &B);
+    if (rc != WD_OK) return rc;
+    const size_t nb = sizeof(float) * PTC_FLOATS;
+    WD_CUDA(h, cudaMemcpy(B.w, w, nb, where == WD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+    WD_CUDA(h, cudaMemset(B.m, 0, nb));
+    WD_CUDA(h, cudaMemset(B.v, 0, nb));
+    k_round_bf16<<<(PTC_FLOATS + 255) / 256, 256>>>(PTC_FLOATS, B.w, B.weff);
+    WD_CUDA(h, cudaGetLastError());
+    WD_CUDA(h, cudaDeviceSynchronize());
+    h->have_precond = true;
+    h->adam_t = 0;
+    return WD_OK;
+}
+
+extern "C" int wd_precond_get(wd_handle* h, float* w, int where) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!w || (where != WD_HOST && where != WD_DEVICE)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_get: bad argument");
+    if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
+    PtcBufs B;
+    int rc = ptc_bufs(h, &B);
+    if (rc != WD_OK) return rc;
+    WD_CUDA(h, cudaMemcpy(w, B.w, sizeof(float) * PTC_FLOATS,
+                          where == WD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice));
+    return WD_OK;
+}
+
+extern "C" int wd_precond_apply(wd_handle* h, int prec, const void* in, void* out, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if ((prec != WD_FP32 && prec != WD_FP16) || !in || !out || in == out)
+        return fail(h, WD_ERR_INVALID_ARG, "wd_precond_apply: bad argument");
+    if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
+    PtcBufs B;
+    int rc = ptc_bufs(h, &B);
+    if (rc != WD_OK) return rc;
+    const uint4 *le, *lo;
+    if ((rc = ensure_links(h, prec, prec == WD_FP32 ? 18 : 12, &le, &lo)) != WD_OK) return rc;
+    uint4* H = ptc_hidden(h, prec == WD_FP32 ? WD_FP32 : WD_BF16, prec == WD_FP32 ? "ptc.h32" : "ptc.h16");
+    if (!H) return fail(h, WD_ERR_CUDA, "out of device memory");
+    WD_CUDA(h, ptc_apply_raw(h, prec, (const uint4*)in, (uint4*)out, H, B.weff, le, lo, (cudaStream_t)stream, nullptr));
+    return WD_OK;
+}
+
+extern "C" int wd_precond_grad(wd_handle* h, int n, const float* v, const float* y, double mu, float* grad,
+                               double* loss, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (n < 1 || !v || !y || !(mu >= 0)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_grad: bad argument");
+    if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ptc_grad(h, n, v, y, mu, loss, s);
+    if (rc != WD_OK) return rc;
+    if (grad) {
+        PtcBufs B;
+        if ((rc = ptc_bufs(h, &B)) != WD_OK) return rc;
+        WD_CUDA(h, cudaMemcpyAsync(grad, B.grad, sizeof(float) * PTC_FLOATS, cudaMemcpyDeviceToDevice, s));
+        WD_CUDA(h, cudaStreamSynchronize(s));
+    }
+    return WD_OK;
+}
+
+extern "C" int wd_precond_train_step(wd_handle* h, int n, const float* v, const float* y, double mu, double lr,
+                                     double* loss, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (n < 1 || !v || !y || !(mu >= 0) || !(lr > 0)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_train_step: bad argument");
+    if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ptc_grad(h, n, v, y, mu, loss, s);
+    if (rc != WD_OK) return rc;
+    PtcBufs B;
+    if ((rc = ptc_bufs(h, &B)) != WD_OK) return rc;
+    h->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)h->adam_t), c2 = 1.f - std::pow(b2, (float)h->adam_t);
+    k_adam<<<(PTC_FLOATS + 255) / 256, 256, 0, s>>>(PTC_FLOATS, B.w, B.grad, B.m, B.v, (float)lr, b1, b2, 1e-8f, c1,
+                                                   c2, B.weff);
+    WD_CUDA(h, cudaGetLastError());
+    WD_CUDA(h, cudaStreamSynchronize(s));
+    return WD_OK;
+}
+
+namespace wd {
+// BF16-rounded weights used by the kernels (device), or null when none are loaded.
+const float* ptc_weights(wd_handle* h) {
+    if (!h->have_precond) return nullptr;
+    PtcBufs B;
+    if (ptc_bufs(h, &B) != WD_OK) return nullptr;
+    return B.weff;
+}
+}  // namespace wd

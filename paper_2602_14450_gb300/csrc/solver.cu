@@ -26,11 +26,18 @@ namespace wd {
 struct SchemeCfg {
     int prec;          // inner storage precision
     bool fp64_inner;   // WD_FP64_BICGSTAB: the "inner" solve is the whole solve
+    bool learned;      // inner BiCGStab on A M with the learned right preconditioner
 };
 
+cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* H, const float* w,
+                          const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard);
+const float* ptc_weights(wd_handle* h);
+
 static bool scheme_cfg(int scheme, SchemeCfg* c) {
+    c->learned = scheme == WD_MIXED_FP16_LEARNED;
     switch (scheme) {
     case WD_FP64_BICGSTAB: c->prec = WD_FP64; c->fp64_inner = true; return true;
+    case WD_MIXED_FP16_LEARNED: c->prec = WD_FP16; c->fp64_inner = false; return true;
     case WD_MIXED_FP32: c->prec = WD_FP32; c->fp64_inner = false; return true;
     case WD_MIXED_FP16_PLAIN: c->prec = WD_FP16; c->fp64_inner = false; return true;
     case WD_MIXED_FP16: c->prec = WD_FP16; c->fp64_inner = false; return true;
@@ -59,12 +66,18 @@ struct Sys {
     long long vs64 = 0, vs = 0; // units per right-hand side
     uint4 *eta_e, *eta_o, *bhat, *x64, *r64, *tmp64, *xo;             // FP64, nrhs each
     uint4 *r, *rs, *p, *v, *t, *xt, *tmp;                              // inner precision, nrhs each
+    uint4 *phat = nullptr, *shat = nullptr, *H = nullptr;              // M p, M s, hidden channels
+    const float* w = nullptr;                                          // preconditioner weights
     std::vector<double> eta_norm;
     std::vector<bool> active;
 };
 
-static int prepare(Sys& S, int prec, int recon_lo) {
+static int prepare(Sys& S, int prec, int recon_lo, bool learned) {
     wd_handle* h = S.h;
+    if (learned) {
+        if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "learned scheme: no preconditioner weights loaded");
+        if (S.nrhs != 1) return fail(h, WD_ERR_INVALID_ARG, "learned scheme: one right-hand side per lattice");
+    }
     int rc = ensure_solver_state(h, S.nrhs);
     if (rc != WD_OK) return rc;
     if ((rc = ensure_links(h, WD_FP64, 18, &S.le64, &S.lo64)) != WD_OK) return rc;
@@ -84,6 +97,13 @@ static int prepare(Sys& S, int prec, int recon_lo) {
     for (int i = 0; i < 7; ++i) {
         *flo[i] = (uint4*)workspace(h, pre + nlo[i], blo);
         if (!*flo[i]) return fail(h, WD_ERR_CUDA, "out of device memory (%s)", nlo[i]);
+    }
+    if (learned) {
+        S.phat = (uint4*)workspace(h, pre + "phat", blo);
+        S.shat = (uint4*)workspace(h, pre + "shat", blo);
+        S.H = (uint4*)workspace(h, "ptc.h16", vec_bytes(h, WD_BF16) * 2 * 12);
+        S.w = ptc_weights(h);
+        if (!S.phat || !S.shat || !S.H || !S.w) return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
     }
     const size_t lexb = (size_t)S.nrhs * 2 * h->g.Vh * 24 * sizeof(double);
     S.bl = const_cast<double*>(S.b);
@@ -128,8 +148,10 @@ static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, 
 }
 
 // Enqueue one inner BiCGStab iteration (Alg. 3 / Alg. 4 loop body) of every
-// right-hand side of a system.
-static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool scale_pass, cudaStream_t s) {
+// right-hand side of a system; with a right preconditioner M the operator is
+// A M: v = A (M p), t = A (M s), x += lambda'/gamma' (omega M s + alpha M p).
+static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool scale_pass, bool learned,
+                                     cudaStream_t s) {
     const int n = S.h->g.Vh, nr = S.nrhs;
     const long long vs = S.vs;
     const double k2 = S.h->kappa * S.h->kappa;
@@ -142,25 +164,36 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         P.vs = vs;
         // p := beta (p - omega' v) + r   (gamma of p and v folded in)
         if ((e = Ops<T>::pupdate(n, nr, vs, S.p, S.v, S.r, st, s)) != cudaSuccess) return e;
+        const uint4* pa = S.p;   // operand of A
+        if (learned) {
+            if ((e = ptc_apply_raw(h, WD_FP16, S.p, S.phat, S.H, S.w, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            pa = S.phat;
+        }
         // v = A p = p - kappa^2 H_eo H_oe p ; alpha = rho / (r*, v)
-        P.parity = 1; P.links = S.lo; P.in = S.p; P.out = S.tmp; P.a = 1.0;
+        P.parity = 1; P.links = S.lo; P.in = pa; P.out = S.tmp; P.a = 1.0;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.v; P.y = S.p; P.a = -k2; P.b = 1.0;
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.v; P.y = pa; P.a = -k2; P.b = 1.0;
         P.rstar = S.rs; P.rc = red_ctx(h, ST_ALPHA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_RSV, P, s)) != cudaSuccess) return e;
         // r := r - alpha v
         if ((e = Ops<T>::supdate(n, nr, vs, S.r, S.v, st, s)) != cudaSuccess) return e;
-        // t = A r ; omega from (t, r), (t, t), (r, r)
+        const uint4* sa = S.r;   // operand of A
+        if (learned) {
+            if ((e = ptc_apply_raw(h, WD_FP16, S.r, S.shat, S.H, S.w, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            sa = S.shat;
+        }
+        // t = A s ; omega from (t, s), (t, t), (s, s)
         P.rc = red_ctx(h, ST_NONE);
-        P.parity = 1; P.links = S.lo; P.in = S.r; P.out = S.tmp; P.y = nullptr; P.a = 1.0; P.b = 0.0;
+        P.parity = 1; P.links = S.lo; P.in = sa; P.out = S.tmp; P.y = nullptr; P.a = 1.0; P.b = 0.0;
         P.rstar = nullptr;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.t; P.y = S.r; P.a = -k2; P.b = 1.0;
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.t; P.y = sa; P.a = -k2; P.b = 1.0;
+        P.rstar = learned ? S.r : nullptr;   // dot partner s when t = A M s
         P.rc = red_ctx(h, ST_OMEGA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_TS, P, s)) != cudaSuccess) return e;
-        // x += lambda'/gamma' (omega r + alpha p) ; r := r - omega t ; |r|, |x|
-        if ((e = Ops<T>::xr(!scale_pass, n, nr, vs, S.xt, S.r, S.p, S.t, S.rs, st, red_ctx(h, ST_RNORM), s)) !=
-            cudaSuccess)
+        // x += lambda'/gamma' (omega s + alpha p) ; r := s - omega t ; |r|, |x|
+        if ((e = Ops<T>::xr(!scale_pass, n, nr, vs, S.xt, S.r, S.p, S.t, S.rs, learned ? S.shat : nullptr,
+                            learned ? S.phat : nullptr, st, red_ctx(h, ST_RNORM), s)) != cudaSuccess)
             return e;
         // r := (sigma / g) r ; gamma ; [x := lambda x] ; next rho, beta
         if (scale_pass)
@@ -170,7 +203,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
 }
 
 // Capture `iters` iterations of every system plus the activity flag.
-static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_pass, int iters,
+static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_pass, bool learned, int iters,
                          cudaGraphExec_t* out) {
     wd_handle* h0 = sys[0].h;
     cudaGraph_t graph = nullptr;
@@ -178,7 +211,7 @@ static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < iters && e == cudaSuccess; ++i)
         for (auto& S : sys)
-            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, scale_pass, h0->cap);
+            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, scale_pass, learned, h0->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(h0->dflag, 0, sizeof(int), h0->cap);
     for (auto& S : sys) {
         if (e != cudaSuccess) break;
@@ -234,7 +267,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
     const int recon_lo = cfg.fp64_inner ? 18 : prm.recon;
     const bool scale_pass = prm.sigma > 0 || prm.rescale_x;
     const int ips = prm.iters_per_sync;
-    const int kpi = scale_pass ? 8 : 7;   // kernels per inner iteration
+    const int kpi = (scale_pass ? 8 : 7) + (cfg.learned ? 4 : 0);   // kernels per inner iteration
 
     std::vector<Sys> sys;
     int total_rhs = 0;
@@ -250,7 +283,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             if (o.h == S.h) return fail(S.h, WD_ERR_INVALID_ARG, "a handle appears twice in one batch");
         S.b_dev = is_device_ptr(S.b);
         S.x_dev = is_device_ptr(S.x);
-        int rc = prepare(S, prec, recon_lo);
+        int rc = prepare(S, prec, recon_lo, cfg.learned);
         if (rc != WD_OK) return rc;
         sys.push_back(S);
         total_rhs += S.nrhs;
@@ -302,16 +335,16 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
     cudaGraphExec_t exec = nullptr;
     bool own_exec = false;
     if (sys.size() == 1) {
-        GraphKey key{prec, recon_lo, scale_pass ? 1 : 0, ips, sys[0].nrhs, h0->gen};
+        GraphKey key{prec, recon_lo, (scale_pass ? 1 : 0) | (cfg.learned ? 2 : 0), ips, sys[0].nrhs, h0->gen};
         auto it = h0->graphs.find(key);
         if (it != h0->graphs.end()) {
             exec = it->second;
         } else {
-            if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, ips, &exec)) != WD_OK) return rc;
+            if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, cfg.learned, ips, &exec)) != WD_OK) return rc;
             h0->graphs[key] = exec;
         }
     } else {
-        if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, ips, &exec)) != WD_OK) return rc;
+        if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, cfg.learned, ips, &exec)) != WD_OK) return rc;
         own_exec = true;
     }
     long long graph_kernels = 0;
@@ -488,6 +521,7 @@ extern "C" int wd_solve_params_default(int scheme, wd_solve_params* p) {
         break;
     case WD_MIXED_FP16:
     case WD_MIXED_BF16:         // Alg. 2 + Alg. 3, Table 2 row s = 128, sigma = 64
+    case WD_MIXED_FP16_LEARNED:
         p->s = 128.0;
         p->sigma = 64.0;
         p->sigma_lambda = 64.0;

@@ -28,8 +28,12 @@ SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_pla
 
 # Exported symbols (the declarations of include/wd.h).
 SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_vector_bytes", "wd_pack",
-           "wd_unpack", "wd_apply", "wd_solve_params_default", "wd_solve", "wd_solve_batch", "wd_status_string",
+           "wd_unpack", "wd_apply", "wd_solve_params_default", "wd_solve", "wd_solve_batch", "wd_precond_set",
+           "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error"]
+WD_MIXED_FP16_LEARNED = 5
+SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
+PRECOND_FLOATS = 6912
 
 
 class SolveParams(C.Structure):
@@ -73,6 +77,11 @@ def lib():
         L.wd_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
         L.wd_solve_batch.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(vp), d, i,
                                      C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
+        L.wd_precond_set.argtypes = [vp, vp, i]
+        L.wd_precond_get.argtypes = [vp, vp, i]
+        L.wd_precond_apply.argtypes = [vp, i, vp, vp, vp]
+        L.wd_precond_grad.argtypes = [vp, i, vp, vp, d, vp, C.POINTER(d), vp]
+        L.wd_precond_train_step.argtypes = [vp, i, vp, vp, d, d, C.POINTER(d), vp]
         L.wd_status_string.argtypes = [i]
         L.wd_status_string.restype = C.c_char_p
         L.wd_last_error.argtypes = [vp]
@@ -161,6 +170,37 @@ class Lattice:
     def apply(self, prec, recon, op, x, y, stream=None):
         self._check(lib().wd_apply(self.h, PREC.get(prec, prec), recon, op, _ptr(x), _ptr(y), _stream(stream)),
                     "wd_apply")
+
+    # --- learned right preconditioner -------------------------------------
+    def precond_set(self, w):
+        """w: float32 tensor of PRECOND_FLOATS weights (flat layout of wd.h), CPU or CUDA."""
+        w = w.to(dtype=__import__("torch").float32).contiguous()
+        self._check(lib().wd_precond_set(self.h, _ptr(w), WD_DEVICE if w.is_cuda else WD_HOST), "wd_precond_set")
+
+    def precond_get(self):
+        import torch
+        w = torch.empty(PRECOND_FLOATS, dtype=torch.float32)
+        self._check(lib().wd_precond_get(self.h, _ptr(w), WD_HOST), "wd_precond_get")
+        return w
+
+    def precond_apply(self, prec, x, y, stream=None):
+        self._check(lib().wd_precond_apply(self.h, PREC.get(prec, prec), _ptr(x), _ptr(y), _stream(stream)),
+                    "wd_precond_apply")
+
+    def precond_grad(self, v, y, mu, stream=None):
+        """(loss, gradient) for n samples: v, y float32 device tensors [n, packed even vector]."""
+        import torch
+        g = torch.empty(PRECOND_FLOATS, dtype=torch.float32, device="cuda")
+        loss = C.c_double()
+        self._check(lib().wd_precond_grad(self.h, int(v.shape[0]), _ptr(v), _ptr(y), float(mu), _ptr(g),
+                                          C.byref(loss), _stream(stream)), "wd_precond_grad")
+        return loss.value, g
+
+    def precond_train_step(self, v, y, mu, lr, stream=None):
+        loss = C.c_double()
+        self._check(lib().wd_precond_train_step(self.h, int(v.shape[0]), _ptr(v), _ptr(y), float(mu), float(lr),
+                                                C.byref(loss), _stream(stream)), "wd_precond_train_step")
+        return loss.value
 
     def solve_rhs(self, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):
         """Several right-hand sides of this lattice in one batched solve; b, x: [nrhs, ...] float64."""

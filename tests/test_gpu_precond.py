@@ -1,0 +1,110 @@
+"""Learned right preconditioner on the GPU against the oracle (forward, gradients),
+training, and the preconditioned solve."""
+
+import pytest
+import torch
+
+from oracle import ptc
+from oracle import solvers as S
+from oracle import wilson as W
+from paper_2602_14450_gb300 import learned, synth, wd
+from tests.gpu_util import from_lex, lattice, lex_dev, rel_l2
+
+pytestmark = pytest.mark.gpu
+BC = (1, 1, 1, -1)
+DIMS = (4, 4, 4, 8)
+KAPPA = 0.12
+
+
+def bf16_weights(seed, scale=0.1):
+    w1, w2 = ptc.random_weights(seed, scale)
+    flat = ptc.to_flat(w1, w2).to(torch.float32)
+    flat = flat.to(torch.bfloat16).to(torch.float32)        # the kernels use BF16-rounded weights
+    return flat, ptc.from_flat(flat)
+
+
+def packed_even(lat, prec, field):
+    buf = torch.empty(lat.vector_bytes(prec), dtype=torch.uint8, device="cuda")
+    lat.pack(prec, 0, lex_dev(field), buf)
+    return buf
+
+
+def unpacked_even(lat, prec, buf, dims):
+    out = torch.zeros(lex_dev(synth.gaussian_source(dims, 0)).shape, dtype=torch.float64, device="cuda")
+    lat.unpack(prec, 0, buf, out)
+    return from_lex(out, dims)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    u = synth.gauge_random(DIMS, 0.5, seed=61)
+    lat = lattice(u, KAPPA, DIMS)
+    return u, lat
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1.5e-2)])
+def test_forward_matches_oracle(setup, prec, tol):
+    u, lat = setup
+    flat, (w1, w2) = bf16_weights(seed=7)
+    lat.precond_set(flat)
+    psi = W.restrict(synth.gaussian_source(DIMS, seed=62), 0)
+    out = torch.empty(lat.vector_bytes(prec), dtype=torch.uint8, device="cuda")
+    lat.precond_apply(prec, packed_even(lat, prec, psi), out)
+    got = unpacked_even(lat, prec, out, DIMS)
+    want = ptc.apply(u, w1, w2, psi, BC)
+    assert rel_l2(got, want) <= tol
+
+
+def test_identity_weights(setup):
+    u, lat = setup
+    w1, w2 = ptc.identity_weights()
+    lat.precond_set(ptc.to_flat(w1, w2).to(torch.float32))
+    psi = W.restrict(synth.gaussian_source(DIMS, seed=63), 0)
+    out = torch.empty(lat.vector_bytes("fp32"), dtype=torch.uint8, device="cuda")
+    lat.precond_apply("fp32", packed_even(lat, "fp32", psi), out)
+    assert rel_l2(unpacked_even(lat, "fp32", out, DIMS), psi) <= 1e-7
+
+
+def test_gradients_match_oracle(setup):
+    u, lat = setup
+    flat, (w1, w2) = bf16_weights(seed=8)
+    lat.precond_set(flat)
+    mu = 0.5
+    vs = [W.restrict(synth.gaussian_source(DIMS, seed=70 + i), 0) for i in range(2)]
+    ys = [W.restrict(synth.gaussian_source(DIMS, seed=80 + i), 0) for i in range(2)]
+    v = torch.stack([packed_even(lat, "fp32", f).view(torch.float32) for f in vs])
+    y = torch.stack([packed_even(lat, "fp32", f).view(torch.float32) for f in ys])
+    loss, g = lat.precond_grad(v, y, mu)
+    # the oracle on the same (FP32-rounded) samples
+    vs32 = [unpacked_even(lat, "fp32", packed_even(lat, "fp32", f), DIMS) for f in vs]
+    ys32 = [unpacked_even(lat, "fp32", packed_even(lat, "fp32", f), DIMS) for f in ys]
+    L, g1, g2 = ptc.grads(u, w1, w2, vs32, ys32, KAPPA, mu, BC)
+    assert abs(loss - L) <= 1e-5 * L
+    want = ptc.to_flat(g1, g2)
+    got = g.cpu().double()
+    assert (torch.linalg.vector_norm(got - want) / torch.linalg.vector_norm(want)).item() <= 1e-4
+
+
+def test_training_lowers_the_loss_and_preconditioned_solve_converges(setup):
+    u, lat = setup
+    w1, w2 = ptc.random_weights(seed=9, scale=0.02)
+    lat.precond_set(ptc.to_flat(w1, w2).to(torch.float32))
+    v, y = learned.make_samples(lat, 8, seed=500)
+    losses = learned.train(lat, v, y, steps=40, lr=3e-3, mu=1.0, batch=4)
+    assert losses[-1] < 0.8 * losses[0]
+    eta = synth.gaussian_source(DIMS, seed=64)
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, 1e-10, "mixed_fp16_learned")
+    assert st.status == wd.WD_OK
+    assert S.norm(eta - W.dirac(u, from_lex(x, DIMS), KAPPA, BC)) / S.norm(eta) <= 1e-10
+
+
+def test_learned_scheme_needs_weights():
+    dims = (4, 4, 4, 4)
+    lat = lattice(synth.gauge_random(dims, 0.5, seed=1), 0.12, dims)
+    b = lex_dev(synth.gaussian_source(dims, seed=2))
+    x = torch.zeros_like(b)
+    with pytest.raises(wd.WDError) as e:
+        lat.solve(b, x, 1e-10, "mixed_fp16_learned")
+    assert e.value.code == wd.WD_ERR_INVALID_ARG
