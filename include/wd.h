@@ -161,6 +161,25 @@ int wd_unpack(wd_handle* h, int prec, int parity, const void* packed, double* le
  * (in and out must not overlap). Arithmetic as in enum wd_prec. */
 int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* out, void* stream);
 
+/* out = in - kappa^2 H_eo H_oe in, exactly as wd_apply(h, prec, recon,
+ * WD_OP_EO_A, ...), for callers that must not allocate device memory (code
+ * that runs under a caching allocator owning all device memory, or code that
+ * must not risk the implicit device synchronization of cudaMalloc/cudaFree).
+ * The paper has no counterpart; it is a service of this library.
+ * - Allocates nothing: the odd-site intermediate lives in a fixed 16 MiB
+ *   array in the library's device memory, held on every GPU that loads the
+ *   library until the process exits. A precision whose odd-site vector
+ *   (wd_vector_bytes) exceeds 16 MiB is refused with WD_ERR_INVALID_ARG
+ *   (FP16: up to 349,525 sites per parity, e.g. 24^3 x 48).
+ * - The links of (prec, recon) must already exist: call wd_apply or wd_solve
+ *   with them once before (building them allocates); otherwise
+ *   WD_ERR_INVALID_ARG.
+ * - The first call on a device looks up the array's device address; make
+ *   that first call outside any stream capture.
+ * - All calls on a device share the array: calls that may overlap on the GPU
+ *   (different streams without ordering) race and give wrong results. */
+int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void* in, void* out, void* stream);
+
 /* Fill `p` with the defaults of `scheme` (Table 2 rows; s = 128, sigma = 64
  * for WD_MIXED_FP16). */
 int wd_solve_params_default(int scheme, wd_solve_params* p);

@@ -28,7 +28,8 @@ SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_pla
 
 # Exported symbols (the declarations of include/wd.h).
 SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_vector_bytes", "wd_pack",
-           "wd_unpack", "wd_apply", "wd_solve_params_default", "wd_solve", "wd_solve_batch", "wd_precond_set",
+           "wd_unpack", "wd_apply", "wd_apply_eo_noalloc", "wd_solve_params_default", "wd_solve", "wd_solve_batch",
+           "wd_precond_set",
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error"]
 WD_MIXED_FP16_LEARNED = 5
@@ -73,6 +74,7 @@ def lib():
         L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
         L.wd_unpack.argtypes = [vp, i, i, vp, vp, vp]
         L.wd_apply.argtypes = [vp, i, i, i, vp, vp, vp]
+        L.wd_apply_eo_noalloc.argtypes = [vp, i, i, vp, vp, vp]
         L.wd_solve_params_default.argtypes = [i, C.POINTER(SolveParams)]
         L.wd_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
         L.wd_solve_batch.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(vp), d, i,
