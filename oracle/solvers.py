@@ -124,6 +124,8 @@ def bicgstab(apply_a, b: torch.Tensor, tol: float, maxiter: int = 100000, x0=Non
         if rn <= tol * bref:
             info.converged = True
             break
+        if not math.isfinite(rn):
+            break
         rho = dot(rhat, r)
         beta = (rho / rho_old) * (alpha / omega)
         p = r + beta * (p - omega * v)

@@ -78,9 +78,56 @@ def restrict(psi: torch.Tensor, p: int) -> torch.Tensor:
     return psi * m[..., None, None]
 
 
-def hop_pq(U, psi, p: int, bc=(1, 1, 1, -1)) -> torch.Tensor:
-    """H restricted to outputs on parity p and inputs on parity 1 - p (H_eo for p = 0)."""
+def hop_pq_full(U, psi, p: int, bc=(1, 1, 1, -1)) -> torch.Tensor:
+    """H restricted to outputs on parity p and inputs on parity 1 - p, via the full-lattice hop."""
     return restrict(hop(U, restrict(psi, 1 - p), bc), p)
+
+
+_TABLES = {}
+
+
+def _parity_tables(dims, p: int, bc):
+    """Lexicographic sites of parity p and, per direction, their neighbours and boundary phases."""
+    key = (tuple(dims), p, tuple(bc))
+    if key not in _TABLES:
+        lx, ly, lz, lt = dims
+        ext = (lx, ly, lz, lt)
+        sites = torch.nonzero(parity(dims).reshape(-1) == p).reshape(-1)
+        c = list(site_coords(dims, sites))
+        lex = lambda cc: cc[0] + lx * (cc[1] + ly * (cc[2] + lz * cc[3]))
+        per_mu = []
+        for mu in range(4):
+            up = [v.clone() for v in c]
+            up[mu] = (c[mu] + 1) % ext[mu]
+            dn = [v.clone() for v in c]
+            dn[mu] = (c[mu] - 1) % ext[mu]
+            ph_up = torch.where(c[mu] == ext[mu] - 1, float(bc[mu]), 1.0).to(CDT)[:, None, None]
+            ph_dn = torch.where(c[mu] == 0, float(bc[mu]), 1.0).to(CDT)[:, None, None]
+            per_mu.append((lex(up), lex(dn), ph_up, ph_dn))
+        _TABLES[key] = (sites, per_mu)
+    return _TABLES[key]
+
+
+def hop_pq(U, psi, p: int, bc=(1, 1, 1, -1)) -> torch.Tensor:
+    """H restricted to outputs on parity p and inputs on parity 1 - p (H_eo for p = 0).
+
+    Eq. 1 evaluated only at the sites of parity p: their neighbours all lie on
+    parity 1 - p, so only that part of psi is read. Same formula as ``hop``.
+    """
+    dims = dims_of(psi)
+    sites, per_mu = _parity_tables(dims, p, bc)
+    pm, pp = projectors()
+    uf = U.reshape(4, -1, 3, 3)
+    pf = psi.reshape(-1, 4, 3)
+    acc = torch.zeros((len(sites), 4, 3), dtype=psi.dtype)
+    for mu in range(4):
+        up, dn, ph_up, ph_dn = per_mu[mu]
+        fwd = (ph_up * pf[up]) @ uf[mu, sites].transpose(-1, -2)
+        bwd = (ph_dn * pf[dn]) @ uf[mu, dn].conj()
+        acc += pm[mu] @ fwd + pp[mu] @ bwd
+    out = torch.zeros_like(pf)
+    out[sites] = acc
+    return out.reshape(psi.shape)
 
 
 def eo_operator(U, psi_e, kappa: float, bc=(1, 1, 1, -1)) -> torch.Tensor:

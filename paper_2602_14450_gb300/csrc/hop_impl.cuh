@@ -142,7 +142,7 @@ __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_U
     }
 }
 
-template <typename T, int R, int EPI, int RED>
+template <typename T, int R, int EPI, int RED, bool PF>
 __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
@@ -178,40 +178,84 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] = 0;
 
+        // neighbour site and wrap flag of each direction d = 2 mu (+mu), 2 mu + 1 (-mu)
+        int hnb[8];
+        bool wrp[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int mu = d >> 1;
+            const bool fwd = (d & 1) == 0;
+            if (mu == 0) {
+                wrp[d] = fwd ? (x == Lx - 1) : (x == 0);
+                const int xn = fwd ? (wrp[d] ? 0 : x + 1) : (wrp[d] ? Lx - 1 : x - 1);
+                hnb[d] = row * Lxh + (xn >> 1);
+            } else if (mu == 1) {
+                wrp[d] = fwd ? (y == Ly - 1) : (y == 0);
+                hnb[d] = fwd ? (wrp[d] ? h - (Ly - 1) * sy : h + sy) : (wrp[d] ? h + (Ly - 1) * sy : h - sy);
+            } else if (mu == 2) {
+                wrp[d] = fwd ? (z == Lz - 1) : (z == 0);
+                hnb[d] = fwd ? (wrp[d] ? h - (Lz - 1) * sz : h + sz) : (wrp[d] ? h + (Lz - 1) * sz : h - sz);
+            } else {
+                wrp[d] = fwd ? (t == Lt - 1) : (t == 0);
+                hnb[d] = fwd ? (wrp[d] ? h - (Lt - 1) * st : h + st) : (wrp[d] ? h + (Lt - 1) * st : h - st);
+            }
+        }
+        // PF: the raw units of the next direction's neighbour and the next link
+        // group are loaded before the current direction is computed.
+        constexpr int SU = Spinor<T>::UNITS;
+        uint4 nbu[2][SU];
+        uint4 lgu[2][LF::GROUP_UNITS];
+        if (PF) {
+#pragma unroll
+            for (int u = 0; u < SU; ++u) nbu[0][u] = __ldg(vin + (size_t)u * Vh + hnb[0]);
+#pragma unroll
+            for (int k = 0; k < LF::GROUP_UNITS; ++k) lgu[0][k] = __ldcs(P.links + (size_t)k * Vh + h);
+        }
+
 #pragma unroll
         for (int grp = 0; grp < 8 / LF::G; ++grp) {
             uint4 lu[LF::GROUP_UNITS];
+            if (PF) {
 #pragma unroll
-            for (int k = 0; k < LF::GROUP_UNITS; ++k)
-                lu[k] = __ldcs(P.links + (size_t)(grp * LF::GROUP_UNITS + k) * Vh + h);
+                for (int k = 0; k < LF::GROUP_UNITS; ++k) lu[k] = lgu[grp & 1][k];
+                if (grp + 1 < 8 / LF::G) {
+#pragma unroll
+                    for (int k = 0; k < LF::GROUP_UNITS; ++k)
+                        lgu[(grp + 1) & 1][k] = __ldcs(P.links + (size_t)((grp + 1) * LF::GROUP_UNITS + k) * Vh + h);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < LF::GROUP_UNITS; ++k)
+                    lu[k] = __ldcs(P.links + (size_t)(grp * LF::GROUP_UNITS + k) * Vh + h);
+            }
 #pragma unroll
             for (int j = 0; j < LF::G; ++j) {
                 const int d = grp * LF::G + j;
                 const int mu = d >> 1;
                 const bool fwd = (d & 1) == 0;
-                int hn;
-                bool wrap;
-                if (mu == 0) {
-                    wrap = fwd ? (x == Lx - 1) : (x == 0);
-                    const int xn = fwd ? (wrap ? 0 : x + 1) : (wrap ? Lx - 1 : x - 1);
-                    hn = row * Lxh + (xn >> 1);
-                } else if (mu == 1) {
-                    wrap = fwd ? (y == Ly - 1) : (y == 0);
-                    hn = fwd ? (wrap ? h - (Ly - 1) * sy : h + sy) : (wrap ? h + (Ly - 1) * sy : h - sy);
-                } else if (mu == 2) {
-                    wrap = fwd ? (z == Lz - 1) : (z == 0);
-                    hn = fwd ? (wrap ? h - (Lz - 1) * sz : h + sz) : (wrap ? h + (Lz - 1) * sz : h - sz);
-                } else {
-                    wrap = fwd ? (t == Lt - 1) : (t == 0);
-                    hn = fwd ? (wrap ? h - (Lt - 1) * st : h + st) : (wrap ? h + (Lt - 1) * st : h - st);
-                }
+                const bool wrap = wrp[d];
                 C nb[24];
-                load_spinor<T>(vin, Vh, hn, nb);
+                if (PF) {
+                    uint4 cur[SU];
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) cur[u] = nbu[d & 1][u];
+                    if (d + 1 < 8) {
+#pragma unroll
+                        for (int u = 0; u < SU; ++u) nbu[(d + 1) & 1][u] = __ldg(vin + (size_t)u * Vh + hnb[d + 1]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < SU; ++u)
+#pragma unroll
+                        for (int i = 0; i < Unit<T>::N; ++i) nb[u * Unit<T>::N + i] = Unit<T>::get(cur[u], i);
+                } else {
+                    load_spinor<T>(vin, Vh, hnb[d], nb);
+                }
                 C hs[12], chi[12];
                 project<C>(mu, fwd, nb, hs);
-                if (wrap && g.bc[mu] < 0) {
+                if (g.bc[mu] < 0) {      // uniform: only antiperiodic directions pay for the phase
+                    const C ph = wrap ? C(-1) : C(1);
 #pragma unroll
-                    for (int i = 0; i < 12; ++i) hs[i] = -hs[i];
+                    for (int i = 0; i < 12; ++i) hs[i] *= ph;
                 }
                 link_mul<T, R>(lu, j * R, hs, chi);
                 reconstruct<C>(mu, fwd, chi, acc);

@@ -30,6 +30,7 @@ struct HopParams {
     RedCtx rc;              // reduction target (partials, ticket, state, stage)
     const SolverState* guard;  // per-rhs state consulted by the guard
     int guard_kind;            // GuardKind
+    int* err;                  // set to 1 by a kernel whose bounded wait gave up (may be null)
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.
@@ -73,9 +74,11 @@ cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* ou
 constexpr int VEC_BLOCK = 256;
 int hop_block();
 void set_hop_block(int b);
-// Hop kernel for FP32-arithmetic storage types: 1 = one site per thread
-// (default), 2 = two sites per thread with packed FP32x2 math. Read once from
-// the environment variable WD_HOP_KERNEL.
+// Hop kernel variant, read once from the environment variable WD_HOP_KERNEL:
+// 4 = one site per thread, neighbour and link loads issued one direction
+// ahead (default); 1 = one site per thread without the look-ahead; for
+// FP32-arithmetic storage 2 = two sites per thread with packed FP32x2 math;
+// for 16-bit storage 3 = tiles staged in shared memory by bulk copies.
 int hop_variant();
 int num_sms();
 

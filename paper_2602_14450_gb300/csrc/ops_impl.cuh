@@ -8,6 +8,7 @@
 
 #include "blas_impl.cuh"
 #include "hop2_impl.cuh"
+#include "hop3_impl.cuh"
 #include "hop_impl.cuh"
 #include "kernels.h"
 
@@ -43,10 +44,51 @@ inline int stream_blocks(int n, int block) {
     return g < 1 ? 1 : (int)g;
 }
 
+// Tiling of the staged hop kernel, or false when its shared memory would not
+// allow two resident blocks per SM.
+template <typename T, int R>
+bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
+    int TR = 0;
+    for (int tr = 1; tr <= g.L[1]; ++tr)
+        if (g.L[1] % tr == 0 && tr * g.Lxh <= 256 && (tr * g.Lxh) % 2 == 0) TR = tr;
+    if (TR == 0) return false;
+    sg->TR = TR;
+    sg->TS = TR * g.Lxh;
+    sg->ntiles = g.Vh / sg->TS;
+    sg->nrows = 5 * TR + 2;
+    sg->spin_units = Spinor<T>::UNITS;
+    sg->link_units = LinkFmt<T, R>::UNITS;
+    const size_t units = (size_t)sg->spin_units * sg->nrows * g.Lxh + (size_t)sg->link_units * sg->TS;
+    *smem = units * 16;
+    sg->bytes = (unsigned)*smem;
+    return *smem <= 113 * 1024;
+}
+
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     const int block = hop_block();
     const int nr = P.nrhs;
+    if constexpr (sizeof(T) == 2) {
+        StageGeom sg;
+        size_t smem = 0;
+        if (hop_variant() == 3 && stage_geom<T, R>(P.g, &sg, &smem)) {   // shared-memory staged tiles
+            static bool attr = false;
+            const void* k3 = (const void*)hop3_kernel<T, R, E, D>;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            int per = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k3, block, smem) != cudaSuccess || per < 1) per = 1;
+            long nb = (long)per * num_sms() / nr;
+            if (nb > sg.ntiles) nb = sg.ntiles;
+            if (nb > MAX_RED_BLOCKS) nb = MAX_RED_BLOCKS;
+            if (nb < 1) nb = 1;
+            hop3_kernel<T, R, E, D><<<(int)nb * nr, block, smem, s>>>(P, sg, P.err);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (!std::is_same<T, double>::value) {
         if (hop_variant() == 2) {   // two sites per thread, packed FP32x2 arithmetic
             const int n = P.g.Vh / 2;
@@ -56,9 +98,15 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
-    const void* k = (const void*)hop_kernel<T, R, E, D>;
+    if (hop_variant() == 4) {   // one site per thread, loads one direction ahead
+        const void* k = (const void*)hop_kernel<T, R, E, D, true>;
+        const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
+        hop_kernel<T, R, E, D, true><<<nb * nr, block, 0, s>>>(P);
+        return cudaGetLastError();
+    }
+    const void* k = (const void*)hop_kernel<T, R, E, D, false>;
     const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
-    hop_kernel<T, R, E, D><<<nb * nr, block, 0, s>>>(P);
+    hop_kernel<T, R, E, D, false><<<nb * nr, block, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -154,3 +154,12 @@ def test_even_odd_solve_equals_lu():
     assert torch.allclose(b[io], torch.zeros(len(io), dtype=CDT))
     rec = w.eo_reconstruct(u, w.restrict(exact, 0), eta, kappa, BC).reshape(-1)
     assert torch.allclose(rec[io], eta.reshape(-1)[io] - doe @ exact.reshape(-1)[ie], atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_parity_hop_equals_masked_full_hop(p):
+    dims = (4, 6, 2, 8)
+    u = synth.gauge_random(dims, 0.5, seed=24)
+    psi = rand_field(dims, 25)
+    for bc in [(1, 1, 1, -1), (-1, 1, -1, 1)]:
+        assert torch.allclose(w.hop_pq(u, psi, p, bc), w.hop_pq_full(u, psi, p, bc), atol=1e-13, rtol=0)
