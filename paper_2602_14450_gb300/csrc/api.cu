@@ -17,7 +17,7 @@ int hop_variant() {
     static int v = 0;
     if (v == 0) {
         const char* e = std::getenv("WD_HOP_KERNEL");
-        v = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 4;
+        v = (e && e[0] >= '1' && e[0] <= '5') ? e[0] - '0' : 4;
     }
     return v;
 }
@@ -221,6 +221,9 @@ int wd_create(const int dims[4], double kappa, const int bc[4], wd_handle** out)
     }
     h->g.Lxh = dims[0] / 2;
     h->g.Vh = (int)(v / 2);
+    h->g.fxh.init(h->g.Lxh);
+    h->g.fy.init(dims[1]);
+    h->g.fz.init(dims[2]);
     h->kappa = kappa;
     cudaGetDevice(&h->device);
     *out = h;

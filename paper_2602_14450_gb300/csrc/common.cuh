@@ -136,21 +136,40 @@ __device__ __forceinline__ void store_spinor(uint4* v, int stride, int h, typena
 
 // --------------------------------------------------------------- geometry ---
 
+// Division of a non-negative int below 2^31 by a fixed divisor d in
+// [1, 2^31) with one high multiply, one add and one shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// Sec. 4): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(m, n) + n) >> l; the sum stays below 2^32 for n < 2^31.
+struct FastDiv {
+    unsigned m;
+    int l;
+    int d;
+    __host__ void init(int divisor) {
+        d = divisor;
+        l = 0;
+        while ((1u << l) < (unsigned)d) ++l;
+        m = (unsigned)((((unsigned long long)1 << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1);
+    }
+    __device__ __forceinline__ int div(int n) const { return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l); }
+};
+
 struct Geom {
     int L[4];    // Lx, Ly, Lz, Lt
     int Lxh;     // Lx / 2
     int Vh;      // V / 2 (sites per parity)
     int bc[4];   // boundary phases, +1 or -1
+    FastDiv fxh, fy, fz;   // division by Lxh, Ly, Lz
 };
 
 // Lexicographic index of site h on parity p.
 __device__ __forceinline__ int lex_of(const Geom& g, int p, int h) {
-    int row = h / g.Lxh;
+    int row = g.fxh.div(h);
     int xh = h - row * g.Lxh;
-    int y = row % g.L[1];
-    int r2 = row / g.L[1];
-    int z = r2 % g.L[2];
-    int t = r2 / g.L[2];
+    int r2 = g.fy.div(row);
+    int y = row - r2 * g.L[1];
+    int t = g.fz.div(r2);
+    int z = r2 - t * g.L[2];
     int x = 2 * xh + ((p + y + z + t) & 1);
     return x + g.L[0] * row;
 }
@@ -161,12 +180,12 @@ struct Coord {
 };
 __device__ __forceinline__ Coord coord_of(const Geom& g, int p, int h) {
     Coord c;
-    c.row = h / g.Lxh;
+    c.row = g.fxh.div(h);
     const int xh = h - c.row * g.Lxh;
-    c.y = c.row % g.L[1];
-    const int r2 = c.row / g.L[1];
-    c.z = r2 % g.L[2];
-    c.t = r2 / g.L[2];
+    const int r2 = g.fy.div(c.row);
+    c.y = c.row - r2 * g.L[1];
+    c.t = g.fz.div(r2);
+    c.z = r2 - c.t * g.L[2];
     c.x = 2 * xh + ((p + c.y + c.z + c.t) & 1);
     return c;
 }

@@ -14,6 +14,8 @@
 // unit load of a warp is one contiguous 512-byte segment.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace wd {
@@ -34,8 +36,14 @@ template <> struct RedSums<RED_NORM> { static constexpr int N = 1; };
 #define RE(s, c) (2 * (3 * (s) + (c)))
 #define IM(s, c) (2 * (3 * (s) + (c)) + 1)
 
+template <typename C> __device__ __forceinline__ C fmac(C a, C b, C c);
+template <> __device__ __forceinline__ float fmac<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fmac<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Half spinor h[spin 0..1][colour][re,im] from the neighbour spinor p for
 // direction mu: projector (1 - gamma_mu) when fwd, (1 + gamma_mu) otherwise.
+// For mu = 3 the projector is 2 P with P a spin selection; the factor 2 is
+// left to reconstruct() (scaling by 2 is exact, so the result is the same).
 template <typename C>
 __device__ __forceinline__ void project(int mu, bool fwd, const C (&p)[24], C (&h)[12]) {
     const C s = fwd ? C(1) : C(-1);
@@ -57,12 +65,12 @@ __device__ __forceinline__ void project(int mu, bool fwd, const C (&p)[24], C (&
             h0i = p[IM(0, c)] + s * p[RE(2, c)];
             h1r = p[RE(1, c)] + s * p[IM(3, c)];
             h1i = p[IM(1, c)] - s * p[RE(3, c)];
-        } else {                // fwd: (2 p2, 2 p3); bwd: (2 p0, 2 p1)
+        } else {                // fwd: (p2, p3); bwd: (p0, p1), times 2 later
             const int a0 = fwd ? 2 : 0, a1 = fwd ? 3 : 1;
-            h0r = p[RE(a0, c)] + p[RE(a0, c)];
-            h0i = p[IM(a0, c)] + p[IM(a0, c)];
-            h1r = p[RE(a1, c)] + p[RE(a1, c)];
-            h1i = p[IM(a1, c)] + p[IM(a1, c)];
+            h0r = p[RE(a0, c)];
+            h0i = p[IM(a0, c)];
+            h1r = p[RE(a1, c)];
+            h1i = p[IM(a1, c)];
         }
         h[2 * c] = h0r;
         h[2 * c + 1] = h0i;
@@ -71,36 +79,83 @@ __device__ __forceinline__ void project(int mu, bool fwd, const C (&p)[24], C (&
     }
 }
 
-// Accumulate the rebuilt four-spinor of chi = U h into acc.
+// The same projection for an FP16 neighbour spinor, on the stored values:
+// each colour's (re, im) pair is one half2 word, so the projector's sums are
+// one rounded half2 add (or fused add of the swapped pair times +-1) per
+// complex number, and only the 12 projected reals are widened to FP32.
+__device__ __forceinline__ __half2 cword(const uint4 (&u)[3], int q) {
+    unsigned w = word_of(u[q >> 2], q & 3);
+    return *reinterpret_cast<__half2*>(&w);
+}
+__device__ __forceinline__ void project_half2(int mu, bool fwd, const uint4 (&u)[3], float (&h)[12]) {
+    const __half2 pm = fwd ? __floats2half2_rn(-1.f, 1.f) : __floats2half2_rn(1.f, -1.f);   // (-s, s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const __half2 p0 = cword(u, c), p1 = cword(u, 3 + c), p2 = cword(u, 6 + c), p3 = cword(u, 9 + c);
+        __half2 a0, a1;
+        if (mu == 0) {          // h0 = p0 + s i p3, h1 = p1 + s i p2
+            a0 = __hfma2(__lowhigh2highlow(p3), pm, p0);
+            a1 = __hfma2(__lowhigh2highlow(p2), pm, p1);
+        } else if (mu == 1) {   // h0 = p0 + s p3, h1 = p1 - s p2
+            a0 = fwd ? __hadd2(p0, p3) : __hsub2(p0, p3);
+            a1 = fwd ? __hsub2(p1, p2) : __hadd2(p1, p2);
+        } else if (mu == 2) {   // h0 = p0 + s i p2, h1 = p1 - s i p3
+            a0 = __hfma2(__lowhigh2highlow(p2), pm, p0);
+            a1 = __hfma2(__lowhigh2highlow(p3), __hneg2(pm), p1);
+        } else {                // fwd: (p2, p3); bwd: (p0, p1), times 2 later
+            a0 = fwd ? p2 : p0;
+            a1 = fwd ? p3 : p1;
+        }
+        h[2 * c] = __low2float(a0);
+        h[2 * c + 1] = __high2float(a0);
+        h[6 + 2 * c] = __low2float(a1);
+        h[6 + 2 * c + 1] = __high2float(a1);
+    }
+}
+
+// acc += f * (rebuilt four-spinor of chi = U h); f carries the boundary
+// phase of the hop and, for mu = 3, the projector's factor 2. Every term is
+// one fused multiply-add.
 template <typename C>
-__device__ __forceinline__ void reconstruct(int mu, bool fwd, const C (&x)[12], C (&acc)[24]) {
-    const C s = fwd ? C(1) : C(-1);
+__device__ __forceinline__ void reconstruct(int mu, bool fwd, C f, const C (&x)[12], C (&acc)[24]) {
+    const C sf = fwd ? f : -f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const C x0r = x[2 * c], x0i = x[2 * c + 1], x1r = x[6 + 2 * c], x1i = x[6 + 2 * c + 1];
         if (mu == 3) {
             const int a0 = fwd ? 2 : 0, a1 = fwd ? 3 : 1;
-            acc[RE(a0, c)] += x0r; acc[IM(a0, c)] += x0i;
-            acc[RE(a1, c)] += x1r; acc[IM(a1, c)] += x1i;
+            acc[RE(a0, c)] = fmac(f, x0r, acc[RE(a0, c)]);
+            acc[IM(a0, c)] = fmac(f, x0i, acc[IM(a0, c)]);
+            acc[RE(a1, c)] = fmac(f, x1r, acc[RE(a1, c)]);
+            acc[IM(a1, c)] = fmac(f, x1i, acc[IM(a1, c)]);
             continue;
         }
-        acc[RE(0, c)] += x0r; acc[IM(0, c)] += x0i;
-        acc[RE(1, c)] += x1r; acc[IM(1, c)] += x1i;
+        acc[RE(0, c)] = fmac(f, x0r, acc[RE(0, c)]);
+        acc[IM(0, c)] = fmac(f, x0i, acc[IM(0, c)]);
+        acc[RE(1, c)] = fmac(f, x1r, acc[RE(1, c)]);
+        acc[IM(1, c)] = fmac(f, x1i, acc[IM(1, c)]);
         if (mu == 0) {          // comp2 = -s i chi1, comp3 = -s i chi0
-            acc[RE(2, c)] += s * x1i; acc[IM(2, c)] -= s * x1r;
-            acc[RE(3, c)] += s * x0i; acc[IM(3, c)] -= s * x0r;
+            acc[RE(2, c)] = fmac(sf, x1i, acc[RE(2, c)]);
+            acc[IM(2, c)] = fmac(-sf, x1r, acc[IM(2, c)]);
+            acc[RE(3, c)] = fmac(sf, x0i, acc[RE(3, c)]);
+            acc[IM(3, c)] = fmac(-sf, x0r, acc[IM(3, c)]);
         } else if (mu == 1) {   // comp2 = -s chi1, comp3 = s chi0
-            acc[RE(2, c)] -= s * x1r; acc[IM(2, c)] -= s * x1i;
-            acc[RE(3, c)] += s * x0r; acc[IM(3, c)] += s * x0i;
+            acc[RE(2, c)] = fmac(-sf, x1r, acc[RE(2, c)]);
+            acc[IM(2, c)] = fmac(-sf, x1i, acc[IM(2, c)]);
+            acc[RE(3, c)] = fmac(sf, x0r, acc[RE(3, c)]);
+            acc[IM(3, c)] = fmac(sf, x0i, acc[IM(3, c)]);
         } else {                // comp2 = -s i chi0, comp3 = s i chi1
-            acc[RE(2, c)] += s * x0i; acc[IM(2, c)] -= s * x0r;
-            acc[RE(3, c)] -= s * x1i; acc[IM(3, c)] += s * x1r;
+            acc[RE(2, c)] = fmac(sf, x0i, acc[RE(2, c)]);
+            acc[IM(2, c)] = fmac(-sf, x0r, acc[IM(2, c)]);
+            acc[RE(3, c)] = fmac(-sf, x1i, acc[RE(3, c)]);
+            acc[IM(3, c)] = fmac(sf, x1r, acc[IM(3, c)]);
         }
     }
 }
 
 // chi_k = M h_k (k = 0, 1) for the link stored at element offset `off` of the
-// group's units.
+// group's units. Each output is one multiply and a chain of fused
+// multiply-adds (no separate adds).
 template <typename T, int R>
 __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_UNITS], int off,
                                          const typename Unit<T>::C (&h)[12], typename Unit<T>::C (&x)[12]) {
@@ -116,10 +171,16 @@ __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_U
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
-            C re = MR(0, b1) * MR(1, b2) - MI(0, b1) * MI(1, b2) - (MR(0, b2) * MR(1, b1) - MI(0, b2) * MI(1, b1));
-            C im = MR(0, b1) * MI(1, b2) + MI(0, b1) * MR(1, b2) - (MR(0, b2) * MI(1, b1) + MI(0, b2) * MR(1, b1));
+            C re = MI(0, b2) * MI(1, b1);
+            re = fmac(-MR(0, b2), MR(1, b1), re);
+            re = fmac(-MI(0, b1), MI(1, b2), re);
+            re = fmac(MR(0, b1), MR(1, b2), re);
+            C nim = MR(0, b2) * MI(1, b1);
+            nim = fmac(MI(0, b2), MR(1, b1), nim);
+            nim = fmac(-MR(0, b1), MI(1, b2), nim);
+            nim = fmac(-MI(0, b1), MR(1, b2), nim);
             m[12 + 2 * b] = re;
-            m[12 + 2 * b + 1] = -im;
+            m[12 + 2 * b + 1] = nim;
         }
 #undef MR
 #undef MI
@@ -128,22 +189,84 @@ __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_U
     for (int k = 0; k < 2; ++k) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            C re = 0, im = 0;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const C mr = m[2 * (3 * a + b)], mi = m[2 * (3 * a + b) + 1];
-                const C hr = h[6 * k + 2 * b], hi = h[6 * k + 2 * b + 1];
-                re += mr * hr - mi * hi;
-                im += mr * hi + mi * hr;
-            }
+            const C* mr = &m[6 * a];
+            const C* hk = &h[6 * k];
+            C re = mr[0] * hk[0];
+            re = fmac(-mr[1], hk[1], re);
+            re = fmac(mr[2], hk[2], re);
+            re = fmac(-mr[3], hk[3], re);
+            re = fmac(mr[4], hk[4], re);
+            re = fmac(-mr[5], hk[5], re);
+            C im = mr[0] * hk[1];
+            im = fmac(mr[1], hk[0], im);
+            im = fmac(mr[2], hk[3], im);
+            im = fmac(mr[3], hk[2], im);
+            im = fmac(mr[4], hk[5], im);
+            im = fmac(mr[5], hk[4], im);
             x[6 * k + 2 * a] = re;
             x[6 * k + 2 * a + 1] = im;
         }
     }
 }
 
+// Epilogue of one output site: out = a * acc + b * y + c * z, rounded to
+// storage and written, and this thread's share of the fused dot products.
+template <typename T, int EPI, int RED>
+__device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, const uint4* vy, const uint4* vz,
+                                             const uint4* vrs, int h, typename Unit<T>::C (&acc)[24],
+                                             typename Unit<T>::C (&part)[RedSums<RED>::N]) {
+    typedef typename Unit<T>::C C;
+    constexpr int NS = RedSums<RED>::N;
+    const int Vh = P.g.Vh;
+    const C ca = (C)P.a, cb = (C)P.b, cc = (C)P.c;
+    C o[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) o[i] = (EPI == EPI_H && P.a == 1.0) ? acc[i] : ca * acc[i];
+    C yv[24];
+    if constexpr (EPI >= EPI_Y) {
+        load_spinor<T>(vy, Vh, h, yv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) o[i] += cb * yv[i];
+    }
+    if constexpr (EPI >= EPI_YZ) {
+        C zv[24];
+        load_spinor<T>(vz, Vh, h, zv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) o[i] += cc * zv[i];
+    }
+    store_spinor<T>(vout, Vh, h, o);
+
+    if constexpr (RED == RED_RSV) {
+        C rs[24];
+        load_spinor<T>(vrs, Vh, h, rs);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {   // conj(rs) * o
+            part[0] += rs[2 * i] * o[2 * i] + rs[2 * i + 1] * o[2 * i + 1];
+            part[1] += rs[2 * i] * o[2 * i + 1] - rs[2 * i + 1] * o[2 * i];
+        }
+    } else if constexpr (RED == RED_TS) {          // (o, q), (o, o), (q, q); q = rstar if given, else y
+        C qv[24];
+        if (vrs) {
+            load_spinor<T>(vrs, Vh, h, qv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) qv[i] = yv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            part[0] += o[2 * i] * qv[2 * i] + o[2 * i + 1] * qv[2 * i + 1];
+            part[1] += o[2 * i] * qv[2 * i + 1] - o[2 * i + 1] * qv[2 * i];
+            part[2] += o[2 * i] * o[2 * i] + o[2 * i + 1] * o[2 * i + 1];
+            part[NS - 1] += qv[2 * i] * qv[2 * i] + qv[2 * i + 1] * qv[2 * i + 1];
+        }
+    } else if constexpr (RED == RED_NORM) {
+#pragma unroll
+        for (int i = 0; i < 24; ++i) part[0] += o[i] * o[i];
+    }
+}
+
 template <typename T, int R, int EPI, int RED, bool PF>
-__global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
+__global__ void __launch_bounds__(256, sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T) == 4 ? 2 : 1) hop_kernel(const HopParams P) {
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
@@ -160,18 +283,17 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
     const int p = P.parity;
     const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3], Lxh = g.Lxh, Vh = g.Vh;
     const int sy = Lxh, sz = Lxh * Ly, st = Lxh * Ly * Lz;
-    const C ca = (C)P.a, cb = (C)P.b, cc = (C)P.c;
     C part[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) part[k] = 0;
 
     for (int h = sl.b * blockDim.x + threadIdx.x; h < Vh; h += sl.nb * blockDim.x) {
-        const int row = h / Lxh;
+        const int row = g.fxh.div(h);
         const int xh = h - row * Lxh;
-        const int y = row % Ly;
-        const int r2 = row / Ly;
-        const int z = r2 % Lz;
-        const int t = r2 / Lz;
+        const int r2 = g.fy.div(row);
+        const int y = row - r2 * Ly;
+        const int t = g.fz.div(r2);
+        const int z = r2 - t * Lz;
         const int x = 2 * xh + ((p + y + z + t) & 1);
 
         C acc[24];
@@ -234,7 +356,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
                 const int mu = d >> 1;
                 const bool fwd = (d & 1) == 0;
                 const bool wrap = wrp[d];
-                C nb[24];
+                C hs[12], chi[12];
                 if (PF) {
                     uint4 cur[SU];
 #pragma unroll
@@ -243,71 +365,208 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
 #pragma unroll
                         for (int u = 0; u < SU; ++u) nbu[(d + 1) & 1][u] = __ldg(vin + (size_t)u * Vh + hnb[d + 1]);
                     }
+                    if constexpr (std::is_same<T, __half>::value) {
+                        project_half2(mu, fwd, cur, hs);
+                    } else {
+                        C nb[24];
 #pragma unroll
-                    for (int u = 0; u < SU; ++u)
+                        for (int u = 0; u < SU; ++u)
 #pragma unroll
-                        for (int i = 0; i < Unit<T>::N; ++i) nb[u * Unit<T>::N + i] = Unit<T>::get(cur[u], i);
+                            for (int i = 0; i < Unit<T>::N; ++i) nb[u * Unit<T>::N + i] = Unit<T>::get(cur[u], i);
+                        project<C>(mu, fwd, nb, hs);
+                    }
                 } else {
+                    C nb[24];
                     load_spinor<T>(vin, Vh, hnb[d], nb);
+                    project<C>(mu, fwd, nb, hs);
+                }
+                link_mul<T, R>(lu, j * R, hs, chi);
+                const C f = (mu == 3 ? C(2) : C(1)) * ((wrap && g.bc[mu] < 0) ? C(-1) : C(1));
+                reconstruct<C>(mu, fwd, f, chi, acc);
+            }
+        }
+
+        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part);
+    }
+
+    if constexpr (RED != RED_NONE) {
+        double v[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
+        grid_reduce<NS>(v, P.rc, sl);
+    }
+}
+
+// ------------------------------------------------ shared-memory ring form ---
+//
+// The same hop with every thread streaming its operands through a private
+// two-slot ring in shared memory: while the directions of one link group are
+// computed from one slot, the asynchronous copies (cp.async, 16 bytes per
+// thread and instruction) of the next group -- or of the first group of the
+// thread's next site -- fill the other. The copies hold no registers, so the
+// prefetch distance grows without lowering occupancy, and the grid-stride loop
+// carries the pipeline across sites. Each thread reads only what it copied
+// itself, so the only synchronisation is cp.async.wait_group.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Neighbour sites of output site h on parity p; returns the mask of the
+// directions d whose hop wraps around the lattice.
+__device__ __forceinline__ unsigned site_neighbours(const Geom& g, int p, int h, int (&nbr)[8]) {
+    const int Lxh = g.Lxh, Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
+    const int row = g.fxh.div(h);
+    const int xh = h - row * Lxh;
+    const int r2 = g.fy.div(row);
+    const int y = row - r2 * Ly;
+    const int t = g.fz.div(r2);
+    const int z = r2 - t * Lz;
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int sy = Lxh, sz = Lxh * Ly, st = Lxh * Ly * Lz;
+    const bool w0 = x == g.L[0] - 1, w1 = x == 0, w2 = y == Ly - 1, w3 = y == 0;
+    const bool w4 = z == Lz - 1, w5 = z == 0, w6 = t == Lt - 1, w7 = t == 0;
+    nbr[0] = row * Lxh + ((w0 ? 0 : x + 1) >> 1);
+    nbr[1] = row * Lxh + ((w1 ? g.L[0] - 1 : x - 1) >> 1);
+    nbr[2] = w2 ? h - (Ly - 1) * sy : h + sy;
+    nbr[3] = w3 ? h + (Ly - 1) * sy : h - sy;
+    nbr[4] = w4 ? h - (Lz - 1) * sz : h + sz;
+    nbr[5] = w5 ? h + (Lz - 1) * sz : h - sz;
+    nbr[6] = w6 ? h - (Lt - 1) * st : h + st;
+    nbr[7] = w7 ? h + (Lt - 1) * st : h - st;
+    return (unsigned)w0 | (unsigned)w1 << 1 | (unsigned)w2 << 2 | (unsigned)w3 << 3 | (unsigned)w4 << 4 |
+           (unsigned)w5 << 5 | (unsigned)w6 << 6 | (unsigned)w7 << 7;
+}
+
+// Whether unit u (N reals) of a neighbour spinor enters the hop in direction
+// d: the t hops project onto two spin components only (+t: spins 2, 3;
+// -t: spins 0, 1), so a unit holding none of those reals is not copied.
+template <int N> __host__ __device__ constexpr bool unit_needed(int d, int u) {
+    return (d >> 1) != 3 || (u * N < ((d & 1) ? 12 : 24) && (u + 1) * N > ((d & 1) ? 0 : 12));
+}
+
+// Copy the operands of link group `grp` of output site h into the ring slot
+// that starts at `dst` (element u of the slot at dst[u * nt]).
+template <typename T, int R>
+__device__ __forceinline__ void issue_group(const uint4* vin, const uint4* links, int Vh, int h, int grp,
+                                            const int (&nbr)[8], uint4* dst, int nt) {
+    typedef LinkFmt<T, R> LF;
+    constexpr int SU = Spinor<T>::UNITS;
+#pragma unroll
+    for (int j = 0; j < LF::G; ++j) {
+        const int d = grp * LF::G + j;
+#pragma unroll
+        for (int u = 0; u < SU; ++u)
+            if (unit_needed<Unit<T>::N>(d, u)) cp_async16(dst + (j * SU + u) * nt, vin + (size_t)u * Vh + nbr[d]);
+    }
+#pragma unroll
+    for (int k = 0; k < LF::GROUP_UNITS; ++k)
+        cp_async16(dst + (LF::G * SU + k) * nt, links + (size_t)(grp * LF::GROUP_UNITS + k) * Vh + h);
+    cp_async_commit();
+}
+
+// Units of 16 bytes per thread and ring slot; the ring kernel runs with a
+// fixed block size so that every shared-memory offset is a constant.
+template <typename T, int R> struct RingFmt {
+    static constexpr int BLOCK = 128;
+    static constexpr int SLOT = LinkFmt<T, R>::G * Spinor<T>::UNITS + LinkFmt<T, R>::GROUP_UNITS;
+    static constexpr int GROUPS = 8 / LinkFmt<T, R>::G;
+    static constexpr size_t SMEM = (size_t)2 * SLOT * 16 * BLOCK;
+};
+
+template <typename T, int R, int EPI, int RED>
+__global__ void __launch_bounds__(RingFmt<T, R>::BLOCK, 6) hop_ring_kernel(const HopParams P) {
+    typedef typename Unit<T>::C C;
+    typedef LinkFmt<T, R> LF;
+    typedef RingFmt<T, R> RF;
+    constexpr int NS = RedSums<RED>::N;
+    constexpr int SU = Spinor<T>::UNITS;
+    constexpr int N = Unit<T>::N;
+    static_assert(RF::GROUPS % 2 == 0, "a site's groups alternate between the two slots");
+    extern __shared__ uint4 ring[];
+    const Slice sl = slice_of(P.nrhs);
+    if (guarded(P.guard ? P.guard + sl.rhs : nullptr, P.guard_kind)) return;
+    const long long ro = (long long)sl.rhs * P.vs;
+    const uint4* __restrict__ vin = P.in + ro;
+    uint4* vout = P.out + ro;
+    const uint4* vy = P.y ? P.y + ro : nullptr;
+    const uint4* vz = P.z ? P.z + ro : nullptr;
+    const uint4* vrs = P.rstar ? P.rstar + ro : nullptr;
+    const Geom& g = P.g;
+    constexpr int nt = RF::BLOCK;
+    const int Vh = g.Vh, p = P.parity;
+    uint4* mine = ring + threadIdx.x;
+    C part[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) part[k] = 0;
+
+    const int stride = sl.nb * nt;
+    int h = sl.b * nt + threadIdx.x;
+    int nbr[8];
+    unsigned wm = 0;
+    if (h < Vh) {
+        wm = site_neighbours(g, p, h, nbr);
+        issue_group<T, R>(vin, P.links, Vh, h, 0, nbr, mine, nt);
+    }
+    while (h < Vh) {
+        C acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0;
+        const int hn = h + stride;
+        int nbn[8];
+        unsigned wmn = 0;
+#pragma unroll
+        for (int grp = 0; grp < RF::GROUPS; ++grp) {
+            uint4* nxt = mine + ((grp + 1) & 1) * RF::SLOT * nt;
+            if (grp + 1 < RF::GROUPS) {
+                issue_group<T, R>(vin, P.links, Vh, h, grp + 1, nbr, nxt, nt);
+            } else if (hn < Vh) {
+                wmn = site_neighbours(g, p, hn, nbn);
+                issue_group<T, R>(vin, P.links, Vh, hn, 0, nbn, nxt, nt);
+            } else {
+                cp_async_commit();          // empty group: the wait below counts the same way
+            }
+            cp_async_wait<1>();
+            const uint4* cur = mine + (grp & 1) * RF::SLOT * nt;
+            uint4 lu[LF::GROUP_UNITS];
+#pragma unroll
+            for (int k = 0; k < LF::GROUP_UNITS; ++k) lu[k] = cur[(LF::G * SU + k) * nt];
+#pragma unroll
+            for (int j = 0; j < LF::G; ++j) {
+                const int d = grp * LF::G + j;
+                const int mu = d >> 1;
+                const bool fwd = (d & 1) == 0;
+                C nb[24];
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    if (unit_needed<N>(d, u)) {
+                        const uint4 w = cur[(j * SU + u) * nt];
+#pragma unroll
+                        for (int i = 0; i < N; ++i) nb[u * N + i] = Unit<T>::get(w, i);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < N; ++i) nb[u * N + i] = 0;
+                    }
                 }
                 C hs[12], chi[12];
                 project<C>(mu, fwd, nb, hs);
-                if (g.bc[mu] < 0) {      // uniform: only antiperiodic directions pay for the phase
-                    const C ph = wrap ? C(-1) : C(1);
-#pragma unroll
-                    for (int i = 0; i < 12; ++i) hs[i] *= ph;
-                }
                 link_mul<T, R>(lu, j * R, hs, chi);
-                reconstruct<C>(mu, fwd, chi, acc);
+                const C f = (mu == 3 ? C(2) : C(1)) * ((((wm >> d) & 1u) && g.bc[mu] < 0) ? C(-1) : C(1));
+                reconstruct<C>(mu, fwd, f, chi, acc);
             }
         }
-
-        // epilogue: out = a * acc + b * y + c * z
-        C o[24];
+        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part);
+        h = hn;
+        wm = wmn;
 #pragma unroll
-        for (int i = 0; i < 24; ++i) o[i] = ca * acc[i];
-        C yv[24];
-        if constexpr (EPI >= EPI_Y) {
-            load_spinor<T>(vy, Vh, h, yv);
-#pragma unroll
-            for (int i = 0; i < 24; ++i) o[i] += cb * yv[i];
-        }
-        if constexpr (EPI >= EPI_YZ) {
-            C zv[24];
-            load_spinor<T>(vz, Vh, h, zv);
-#pragma unroll
-            for (int i = 0; i < 24; ++i) o[i] += cc * zv[i];
-        }
-        store_spinor<T>(vout, Vh, h, o);
-
-        if constexpr (RED == RED_RSV) {
-            C rs[24];
-            load_spinor<T>(vrs, Vh, h, rs);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {   // conj(rs) * o
-                part[0] += rs[2 * i] * o[2 * i] + rs[2 * i + 1] * o[2 * i + 1];
-                part[1] += rs[2 * i] * o[2 * i + 1] - rs[2 * i + 1] * o[2 * i];
-            }
-        } else if constexpr (RED == RED_TS) {          // (o, q), (o, o), (q, q); q = rstar if given, else y
-            C qv[24];
-            if (vrs) {
-                load_spinor<T>(vrs, Vh, h, qv);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 24; ++i) qv[i] = yv[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                part[0] += o[2 * i] * qv[2 * i] + o[2 * i + 1] * qv[2 * i + 1];
-                part[1] += o[2 * i] * qv[2 * i + 1] - o[2 * i + 1] * qv[2 * i];
-                part[2] += o[2 * i] * o[2 * i] + o[2 * i + 1] * o[2 * i + 1];
-                part[NS - 1] += qv[2 * i] * qv[2 * i] + qv[2 * i + 1] * qv[2 * i + 1];
-            }
-        } else if constexpr (RED == RED_NORM) {
-#pragma unroll
-            for (int i = 0; i < 24; ++i) part[0] += o[i] * o[i];
-        }
+        for (int d = 0; d < 8; ++d) nbr[d] = nbn[d];
     }
+    cp_async_wait<0>();
 
     if constexpr (RED != RED_NONE) {
         double v[NS];

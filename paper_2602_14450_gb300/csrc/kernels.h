@@ -78,7 +78,9 @@ void set_hop_block(int b);
 // 4 = one site per thread, neighbour and link loads issued one direction
 // ahead (default); 1 = one site per thread without the look-ahead; for
 // FP32-arithmetic storage 2 = two sites per thread with packed FP32x2 math;
-// for 16-bit storage 3 = tiles staged in shared memory by bulk copies.
+// for 16-bit storage 3 = tiles staged in shared memory by bulk copies and,
+// with 12-real links, 5 = persistent threads streaming their operands through
+// a per-thread two-slot ring of asynchronous copies in shared memory.
 int hop_variant();
 int num_sms();
 

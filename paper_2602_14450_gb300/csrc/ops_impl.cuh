@@ -89,6 +89,22 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
+    if constexpr (sizeof(T) == 2 && R == 12) {
+        if (hop_variant() == 5) {   // per-thread shared-memory ring of asynchronous copies
+            typedef RingFmt<T, R> RF;
+            const void* k5 = (const void*)hop_ring_kernel<T, R, E, D>;
+            int per = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k5, RF::BLOCK, RF::SMEM) != cudaSuccess || per < 1)
+                per = 1;
+            long nb = (long)per * num_sms() / nr;
+            const long need = ((long)P.g.Vh + RF::BLOCK - 1) / RF::BLOCK;
+            if (nb > need) nb = need;
+            if (D != RED_NONE && nb > MAX_RED_BLOCKS) nb = MAX_RED_BLOCKS;
+            if (nb < 1) nb = 1;
+            hop_ring_kernel<T, R, E, D><<<(int)nb * nr, RF::BLOCK, RF::SMEM, s>>>(P);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (!std::is_same<T, double>::value) {
         if (hop_variant() == 2) {   // two sites per thread, packed FP32x2 arithmetic
             const int n = P.g.Vh / 2;

@@ -7,9 +7,11 @@ generator of ``synth``:
 
 * ``8x8x8x8``     links exp(i eps H), eps = 0.5, kappa = 0.12, Gaussian source.
 * ``16x16x16x32`` the same links after 3 APE steps (alpha = 0.5) with SU(3)
-                  reprojection; kappa chosen by ``oracle/calibrate_kappa.py``
-                  so that float64 BiCGStab needs 500-1500 iterations.
-* ``32x32x32x64`` 2,097,152 sites, same generator (own seed) and kappa.
+                  reprojection; kappa chosen by the oracle's calibration so
+                  that float64 BiCGStab needs 500-1500 iterations.
+* ``32x32x32x64`` 2,097,152 sites, same generator (own seed) and the same
+                  kappa rule applied on this lattice (the critical kappa of a
+                  field of equal smoothness is lower on the larger lattice).
 """
 
 from __future__ import annotations
@@ -20,9 +22,9 @@ from . import synth
 
 GAUGE_SEED = 20260214
 SOURCE_SEED = 450
-# Largest kappa of the calibration grid in the 500-1500 iteration window
-# (tests/golden/kappa_calibration.txt, written by oracle/calibrate_kappa.py).
-KAPPA_SMEARED = None
+# Smallest kappa of each calibration grid in the 500-1500 iteration window
+# (tests/golden/kappa_calibration_<lattice>.txt, written by oracle/calibrate_kappa.py).
+KAPPA = {"16x16x16x32": 0.1265, "32x32x32x64": None}
 
 
 @dataclass(frozen=True)
@@ -50,10 +52,10 @@ class Workload:
 def get(name: str) -> Workload:
     if name == "8x8x8x8":
         return Workload(name, (8, 8, 8, 8), False, 0.12, GAUGE_SEED)
-    if KAPPA_SMEARED is None:
-        raise RuntimeError("kappa of the smeared workloads has not been calibrated")
+    if name not in KAPPA:
+        raise KeyError(name)
+    if KAPPA[name] is None:
+        raise RuntimeError(f"kappa of the {name} workload has not been calibrated")
     if name == "16x16x16x32":
-        return Workload(name, (16, 16, 16, 32), True, KAPPA_SMEARED, GAUGE_SEED)
-    if name == "32x32x32x64":
-        return Workload(name, (32, 32, 32, 64), True, KAPPA_SMEARED, GAUGE_SEED + 2)
-    raise KeyError(name)
+        return Workload(name, (16, 16, 16, 32), True, KAPPA[name], GAUGE_SEED)
+    return Workload(name, (32, 32, 32, 64), True, KAPPA[name], GAUGE_SEED + 2)
