@@ -23,6 +23,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one launch of the FP16 12-real hop at 32^3 x 64,
+# from the ncu capture summarised in profiles/hop_fp16_12_32x32x32x64.md; set
+# to None whenever that kernel changes until it is captured again.
+HOP_FP16_12_TRAFFIC = 270_416_896
+
 METRIC = "time to ‖r‖/‖b‖≤1e-10 at 32^3×64, FP16-mixed vs FP64; Dslash GB/s vs HBM peak"
 TOL = 1e-10
 
@@ -37,6 +42,7 @@ def parse():
     ap.add_argument("--dslash-launches", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and FP32-mixed solves")
+    ap.add_argument("--no-studies", action="store_true", help="skip the batched and learned-preconditioner sections")
     return ap.parse_args()
 
 
@@ -267,9 +273,16 @@ def main():
     peak, peak_kind = measured_peaks()
     top = sweep["fp16_12"]
     roof = {"bound": "hbm", "achieved": top["gbs"], "peak": peak, "unit": "GB/s", "frac": top["gbs"] / peak,
-            "traffic": None, "kernel": "hop_kernel<__half,12,EPI_H,RED_NONE> (H_eo, FP16, 12-real links)",
+            "traffic": HOP_FP16_12_TRAFFIC if wl.dims == (32, 32, 32, 64) else None,
+            "kernel": "hop_kernel<__half,12,EPI_H,RED_NONE> (H_eo, FP16, 12-real links)",
             "peak_kind": peak_kind, "bytes_per_site": top["bytes_per_site"], "sites_per_launch": vh,
             "avg_launch_us": top["us"]}
+
+    studies_out = {}
+    if not args.no_studies:
+        from paper_2602_14450_gb300 import studies
+        studies_out["batched"] = studies.batched(workloads.KAPPA["16x16x16x32"], TOL, stream)
+        studies_out["learned"] = studies.learned_preconditioner(wl.kappa, lat, b, TOL, stream)
 
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -288,6 +301,7 @@ def main():
         "speedup_vs_fp64": (forms["fp64"]["time_s"] / forms["mixed_fp16"]["time_s"]) if "fp64" in forms else None,
         "dslash_sweep": sweep,
         "solve": st.as_dict(),
+        **studies_out,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_iter = stored_oracle_iterations(wl.dims)

@@ -51,39 +51,49 @@ __device__ __forceinline__ void load_link(const uint4* __restrict__ links, int V
     }
 }
 
-// phi = m f on colour for each of the 4 spins (f, phi: [spin][colour][re,im]).
+// phi = m f on colour for each of the 4 spins (f, phi: [spin][colour][re,im]);
+// each output is one multiply and a chain of fused multiply-adds.
 __device__ __forceinline__ void colour_mul(const float (&m)[18], const float (&f)[24], float (&phi)[24]) {
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float re = 0.f, im = 0.f;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const float mr = m[2 * (3 * a + b)], mi = m[2 * (3 * a + b) + 1];
-                const float fr = f[2 * (3 * s + b)], fi = f[2 * (3 * s + b) + 1];
-                re += mr * fr - mi * fi;
-                im += mr * fi + mi * fr;
-            }
+            const float* mr = &m[6 * a];
+            const float* fs = &f[6 * s];
+            float re = mr[0] * fs[0];
+            re = __fmaf_rn(-mr[1], fs[1], re);
+            re = __fmaf_rn(mr[2], fs[2], re);
+            re = __fmaf_rn(-mr[3], fs[3], re);
+            re = __fmaf_rn(mr[4], fs[4], re);
+            re = __fmaf_rn(-mr[5], fs[5], re);
+            float im = mr[0] * fs[1];
+            im = __fmaf_rn(mr[1], fs[0], im);
+            im = __fmaf_rn(mr[2], fs[3], im);
+            im = __fmaf_rn(mr[3], fs[2], im);
+            im = __fmaf_rn(mr[4], fs[5], im);
+            im = __fmaf_rn(mr[5], fs[4], im);
             phi[2 * (3 * s + a)] = re;
             phi[2 * (3 * s + a) + 1] = im;
         }
 }
 
 // acc += w phi on spin (w: 16 complex [s][t] as float2 in shared memory).
-__device__ __forceinline__ void spin_mul_add(const float2* w, const float (&phi)[24], float (&acc)[24]) {
+__device__ __forceinline__ void spin_mul_add_p(const float2* w, const float* phi, float (&acc)[24]) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const float2 c = w[4 * s + t];
+        for (int a = 0; a < 3; ++a) {
+            const float fr = phi[2 * (3 * t + a)], fi = phi[2 * (3 * t + a) + 1];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float fr = phi[2 * (3 * t + a)], fi = phi[2 * (3 * t + a) + 1];
-                acc[2 * (3 * s + a)] += c.x * fr - c.y * fi;
-                acc[2 * (3 * s + a) + 1] += c.x * fi + c.y * fr;
+            for (int s = 0; s < 4; ++s) {
+                const float2 c = w[4 * s + t];
+                acc[2 * (3 * s + a)] = __fmaf_rn(-c.y, fi, __fmaf_rn(c.x, fr, acc[2 * (3 * s + a)]));
+                acc[2 * (3 * s + a) + 1] = __fmaf_rn(c.y, fr, __fmaf_rn(c.x, fi, acc[2 * (3 * s + a) + 1]));
             }
         }
+}
+__device__ __forceinline__ void spin_mul_add(const float2* w, const float (&phi)[24], float (&acc)[24]) {
+    spin_mul_add_p(w, phi, acc);
 }
 
 // T_k f at site h of parity p, f read from the parity its support lives on.
@@ -185,6 +195,126 @@ __global__ void __launch_bounds__(128) k_ptc_fanin(Geom g, const uint4* H, long 
                 }
                 spin_mul_add(&ws[16 * (k * PTC_C + c)], phi, acc);
             }
+        }
+        store_spinor<TOUT>(out_e, g.Vh, h, acc);
+    }
+}
+
+// ---------------------------------------------------------- collapsed M ---
+//
+// The network has no nonlinearity and its spin weights commute with the
+// colour transports, so its two layers collapse exactly:
+//   M psi = sum_{k2} T_{k2} phi_{k2},  phi_{k2} = sum_{k1} V[k2][k1] T_{k1} psi,
+//   V[k2][k1] = sum_c W2[k2][c] W1[k1][c]   (4x4 spin matrix products).
+// For an even-site input (odd sites zero) only phi_0 = V[0][0] psi on the
+// even sites and phi_{1+d} (d = 0..7) on the odd sites are nonzero, so M is
+// two stencil passes with eight odd-site intermediate fields instead of the
+// twelve hidden channels on both parities. The layered kernels above stay for
+// training, which needs the hidden activations.
+
+// V[k2][k1][s][t] from the BF16-rounded weights (double accumulation).
+__global__ void k_ptc_collapse(const float* w, float2* V) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 81 * 16; i += gridDim.x * blockDim.x) {
+        const int k2 = i / 144, k1 = (i / 16) % 9, s = (i / 4) % 4, t = i % 4;
+        double re = 0.0, im = 0.0;
+        for (int c = 0; c < PTC_C; ++c)
+            for (int u = 0; u < 4; ++u) {
+                const float* a = w + 2 * PTC_LAYER + 2 * ((k2 * PTC_C + c) * 16 + 4 * s + u);
+                const float* b = w + 2 * ((k1 * PTC_C + c) * 16 + 4 * u + t);
+                re += (double)a[0] * b[0] - (double)a[1] * b[1];
+                im += (double)a[0] * b[1] + (double)a[1] * b[0];
+            }
+        V[i] = make_float2((float)re, (float)im);
+    }
+}
+
+constexpr int S1_SITES = 32;                // sites per block of the first pass
+constexpr int S1_STRIDE = 8 * 24 + 1;       // floats per site of its transport tile (padded)
+constexpr int S1_VROW = 8 * 16 + 1;         // float2 per k2 row of its V tile (padded)
+
+// First pass on the odd sites y: the eight transports T_{1+d} psi(y) (warp mu
+// computes directions 2 mu and 2 mu + 1 for the block's 32 sites) go to shared
+// memory; then warp mu forms phi_{1+d}(y) = sum_{k1} V[1+d][k1] T_{k1} psi(y)
+// for its two directions and stores them.
+template <typename TIN, typename TPHI, typename LT, int R>
+__global__ void __launch_bounds__(128) k_ptc_s1(Geom g, const uint4* in_e, uint4* phi, long long pvs,
+                                                const uint4* links_o, const float2* V, const SolverState* guard) {
+    if (guarded(guard, GUARD_INNER)) return;
+    __shared__ float ts[S1_SITES * S1_STRIDE];
+    __shared__ float2 vs[8 * S1_VROW];
+    for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+        const int a = i / 128, b = i % 128;     // a = k2 - 1, b = 16 (k1 - 1) + e
+        vs[a * S1_VROW + b] = V[((1 + a) * 9 + 1 + b / 16) * 16 + b % 16];
+    }
+    __syncthreads();
+    const int mu = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* mine = ts + lane * S1_STRIDE;
+    for (int base = blockIdx.x * S1_SITES; base < g.Vh; base += gridDim.x * S1_SITES) {
+        const int h = base + lane;
+        const bool ok = h < g.Vh;
+        if (ok) {
+            const Coord co = coord_of(g, 1, h);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int d = 2 * mu + j;
+                bool wrap;
+                const int hn = neighbour(g, h, co, d, &wrap);
+                float f[24], m[18], t[24];
+                load_spinor<TIN>(in_e, g.Vh, hn, f);
+                if (wrap && g.bc[mu] < 0) {
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) f[i] = -f[i];
+                }
+                load_link<LT, R>(links_o, g.Vh, h, d, m);
+                colour_mul(m, f, t);
+#pragma unroll
+                for (int i = 0; i < 24; ++i) mine[d * 24 + i] = t[i];
+            }
+        }
+        __syncthreads();
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int d2 = 2 * mu + j;
+                float acc[24];
+#pragma unroll
+                for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+#pragma unroll 1
+                for (int k1 = 0; k1 < 8; ++k1) spin_mul_add_p(&vs[d2 * S1_VROW + 16 * k1], mine + 24 * k1, acc);
+                store_spinor<TPHI>(phi + (size_t)d2 * pvs, g.Vh, h, acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Second pass on the even sites x: M psi(x) = V[0][0] psi(x) + sum_d T_{1+d} phi_{1+d}(x).
+template <typename TIN, typename TPHI, typename TOUT, typename LT, int R>
+__global__ void __launch_bounds__(128) k_ptc_s2(Geom g, const uint4* in_e, const uint4* phi, long long pvs,
+                                                uint4* out_e, const uint4* links_e, const float2* V,
+                                                const SolverState* guard) {
+    if (guarded(guard, GUARD_INNER)) return;
+    __shared__ float2 v00[16];
+    if (threadIdx.x < 16) v00[threadIdx.x] = V[threadIdx.x];
+    __syncthreads();
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+        const Coord co = coord_of(g, 0, h);
+        float acc[24], f[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+        load_spinor<TIN>(in_e, g.Vh, h, f);
+        spin_mul_add(v00, f, acc);
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            bool wrap;
+            const int hn = neighbour(g, h, co, d, &wrap);
+            float m[18], t[24];
+            load_spinor<TPHI>(phi + (size_t)d * pvs, g.Vh, hn, f);
+            load_link<LT, R>(links_e, g.Vh, h, d, m);
+            colour_mul(m, f, t);
+            const float ph = (wrap && g.bc[d >> 1] < 0) ? -1.f : 1.f;
+#pragma unroll
+            for (int i = 0; i < 24; ++i) acc[i] = __fmaf_rn(ph, t[i], acc[i]);
         }
         store_spinor<TOUT>(out_e, g.Vh, h, acc);
     }
@@ -324,6 +454,7 @@ static int grid_for(int n, int block) {
 
 struct PtcBufs {
     float *w, *weff, *m, *v, *grad, *wadj;
+    float2* V;      // collapsed spin weights V[k2][k1][s][t] of weff
 };
 
 static int ptc_bufs(wd_handle* h, PtcBufs* b) {
@@ -334,7 +465,9 @@ static int ptc_bufs(wd_handle* h, PtcBufs* b) {
     b->v = (float*)workspace(h, "ptc.v", nb);
     b->grad = (float*)workspace(h, "ptc.grad", nb);
     b->wadj = (float*)workspace(h, "ptc.wadj", nb / 2);
-    if (!b->w || !b->weff || !b->m || !b->v || !b->grad || !b->wadj) return fail(h, WD_ERR_CUDA, "out of device memory");
+    b->V = (float2*)workspace(h, "ptc.V", sizeof(float2) * 81 * 16);
+    if (!b->w || !b->weff || !b->m || !b->v || !b->grad || !b->wadj || !b->V)
+        return fail(h, WD_ERR_CUDA, "out of device memory");
     return WD_OK;
 }
 
@@ -358,6 +491,34 @@ cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_
         k_ptc_fanout<__half, __nv_bfloat16, __half, 12><<<dim3(gx, PTC_C, 2), blk, 0, s>>>(g, in_e, nullptr, H, hvs,
                                                                                          le, lo, w, guard);
         k_ptc_fanin<__nv_bfloat16, __half, __half, 12><<<gx, blk, 0, s>>>(g, H, hvs, out_e, le, w + 2 * PTC_LAYER, guard);
+    }
+    return cudaGetLastError();
+}
+
+// Intermediate fields phi_{1+d} of the collapsed M: 8 odd-site vectors in the
+// storage type of `prec` (FP32 for WD_FP32, BF16 otherwise).
+static uint4* ptc_phi(wd_handle* h, int prec) {
+    return prec == WD_FP32 ? (uint4*)workspace(h, "ptc.phi32", vec_bytes(h, WD_FP32) * 8)
+                           : (uint4*)workspace(h, "ptc.phi16", vec_bytes(h, WD_BF16) * 8);
+}
+
+// out = M in through the collapsed form: FP32 path (FP32 fields, FP32 18-real
+// links) or FP16 path (FP16 in/out, BF16 phi, FP16 12-real links).
+cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* PHI, const float2* V,
+                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard) {
+    const Geom& g = h->g;
+    long long groups = ((long long)g.Vh + S1_SITES - 1) / S1_SITES;
+    const long long cap = (long long)num_sms() * 6;
+    const int g1 = (int)(groups < cap ? groups : cap);
+    const int g2 = grid_for(g.Vh, 128);
+    if (prec == WD_FP32) {
+        const long long pvs = (long long)spinor_units(WD_FP32) * g.Vh;
+        k_ptc_s1<float, float, float, 18><<<g1, 128, 0, s>>>(g, in_e, PHI, pvs, lo, V, guard);
+        k_ptc_s2<float, float, float, float, 18><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
+    } else {
+        const long long pvs = (long long)spinor_units(WD_BF16) * g.Vh;
+        k_ptc_s1<__half, __nv_bfloat16, __half, 12><<<g1, 128, 0, s>>>(g, in_e, PHI, pvs, lo, V, guard);
+        k_ptc_s2<__half, __nv_bfloat16, __half, __half, 12><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
     }
     return cudaGetLastError();
 }
@@ -469,6 +630,7 @@ extern "C" int wd_precond_set(wd_handle* h, const float* w, int where) {
     WD_CUDA(h, cudaMemset(B.m, 0, nb));
     WD_CUDA(h, cudaMemset(B.v, 0, nb));
     k_round_bf16<<<(PTC_FLOATS + 255) / 256, 256>>>(PTC_FLOATS, B.w, B.weff);
+    k_ptc_collapse<<<6, 256>>>(B.weff, B.V);
     WD_CUDA(h, cudaGetLastError());
     WD_CUDA(h, cudaDeviceSynchronize());
     h->have_precond = true;
@@ -498,9 +660,9 @@ extern "C" int wd_precond_apply(wd_handle* h, int prec, const void* in, void* ou
     if (rc != WD_OK) return rc;
     const uint4 *le, *lo;
     if ((rc = ensure_links(h, prec, prec == WD_FP32 ? 18 : 12, &le, &lo)) != WD_OK) return rc;
-    uint4* H = ptc_hidden(h, prec == WD_FP32 ? WD_FP32 : WD_BF16, prec == WD_FP32 ? "ptc.h32" : "ptc.h16");
-    if (!H) return fail(h, WD_ERR_CUDA, "out of device memory");
-    WD_CUDA(h, ptc_apply_raw(h, prec, (const uint4*)in, (uint4*)out, H, B.weff, le, lo, (cudaStream_t)stream, nullptr));
+    uint4* PHI = ptc_phi(h, prec);
+    if (!PHI) return fail(h, WD_ERR_CUDA, "out of device memory");
+    WD_CUDA(h, ptc_apply_m(h, prec, (const uint4*)in, (uint4*)out, PHI, B.V, le, lo, (cudaStream_t)stream, nullptr));
     return WD_OK;
 }
 
@@ -536,17 +698,21 @@ extern "C" int wd_precond_train_step(wd_handle* h, int n, const float* v, const 
     const float c1 = 1.f - std::pow(b1, (float)h->adam_t), c2 = 1.f - std::pow(b2, (float)h->adam_t);
     k_adam<<<(PTC_FLOATS + 255) / 256, 256, 0, s>>>(PTC_FLOATS, B.w, B.grad, B.m, B.v, (float)lr, b1, b2, 1e-8f, c1,
                                                    c2, B.weff);
+    k_ptc_collapse<<<6, 256, 0, s>>>(B.weff, B.V);
     WD_CUDA(h, cudaGetLastError());
     WD_CUDA(h, cudaStreamSynchronize(s));
     return WD_OK;
 }
 
 namespace wd {
-// BF16-rounded weights used by the kernels (device), or null when none are loaded.
-const float* ptc_weights(wd_handle* h) {
+// Collapsed spin weights of the loaded network (device), or null when none are loaded.
+const float2* ptc_collapsed(wd_handle* h) {
     if (!h->have_precond) return nullptr;
     PtcBufs B;
     if (ptc_bufs(h, &B) != WD_OK) return nullptr;
-    return B.weff;
+    return B.V;
 }
+
+// Intermediate fields of the collapsed M for the FP16 solve path.
+uint4* ptc_phi16(wd_handle* h) { return ptc_phi(h, WD_FP16); }
 }  // namespace wd

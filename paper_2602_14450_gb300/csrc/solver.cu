@@ -29,9 +29,10 @@ struct SchemeCfg {
     bool learned;      // inner BiCGStab on A M with the learned right preconditioner
 };
 
-cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* H, const float* w,
-                          const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard);
-const float* ptc_weights(wd_handle* h);
+cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* PHI, const float2* V,
+                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard);
+const float2* ptc_collapsed(wd_handle* h);
+uint4* ptc_phi16(wd_handle* h);
 
 static bool scheme_cfg(int scheme, SchemeCfg* c) {
     c->learned = scheme == WD_MIXED_FP16_LEARNED;
@@ -66,8 +67,8 @@ struct Sys {
     long long vs64 = 0, vs = 0; // units per right-hand side
     uint4 *eta_e, *eta_o, *bhat, *x64, *r64, *tmp64, *xo;             // FP64, nrhs each
     uint4 *r, *rs, *p, *v, *t, *xt, *tmp;                              // inner precision, nrhs each
-    uint4 *phat = nullptr, *shat = nullptr, *H = nullptr;              // M p, M s, hidden channels
-    const float* w = nullptr;                                          // preconditioner weights
+    uint4 *phat = nullptr, *shat = nullptr, *PHI = nullptr;            // M p, M s, fields of the collapsed M
+    const float2* V = nullptr;                                         // collapsed preconditioner weights
     std::vector<double> eta_norm;
     std::vector<bool> active;
 };
@@ -101,9 +102,9 @@ static int prepare(Sys& S, int prec, int recon_lo, bool learned) {
     if (learned) {
         S.phat = (uint4*)workspace(h, pre + "phat", blo);
         S.shat = (uint4*)workspace(h, pre + "shat", blo);
-        S.H = (uint4*)workspace(h, "ptc.h16", vec_bytes(h, WD_BF16) * 2 * 12);
-        S.w = ptc_weights(h);
-        if (!S.phat || !S.shat || !S.H || !S.w) return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
+        S.PHI = ptc_phi16(h);
+        S.V = ptc_collapsed(h);
+        if (!S.phat || !S.shat || !S.PHI || !S.V) return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
     }
     const size_t lexb = (size_t)S.nrhs * 2 * h->g.Vh * 24 * sizeof(double);
     S.bl = const_cast<double*>(S.b);
@@ -166,7 +167,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         if ((e = Ops<T>::pupdate(n, nr, vs, S.p, S.v, S.r, st, s)) != cudaSuccess) return e;
         const uint4* pa = S.p;   // operand of A
         if (learned) {
-            if ((e = ptc_apply_raw(h, WD_FP16, S.p, S.phat, S.H, S.w, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            if ((e = ptc_apply_m(h, WD_FP16, S.p, S.phat, S.PHI, S.V, S.le, S.lo, s, st)) != cudaSuccess) return e;
             pa = S.phat;
         }
         // v = A p = p - kappa^2 H_eo H_oe p ; alpha = rho / (r*, v)
@@ -179,7 +180,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         if ((e = Ops<T>::supdate(n, nr, vs, S.r, S.v, st, s)) != cudaSuccess) return e;
         const uint4* sa = S.r;   // operand of A
         if (learned) {
-            if ((e = ptc_apply_raw(h, WD_FP16, S.r, S.shat, S.H, S.w, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            if ((e = ptc_apply_m(h, WD_FP16, S.r, S.shat, S.PHI, S.V, S.le, S.lo, s, st)) != cudaSuccess) return e;
             sa = S.shat;
         }
         // t = A s ; omega from (t, s), (t, t), (s, s)

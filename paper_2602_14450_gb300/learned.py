@@ -49,3 +49,18 @@ def train(lat: "wd.Lattice", v, y, steps: int, lr: float = 2e-3, mu: float = 1.0
         if log and (k % 10 == 0 or k == steps - 1):
             log(f"step {k}: loss {losses[-1]:.4e}")
     return losses
+
+
+def initial_weights(seed: int, scale: float = 0.02, c_mid: int = 12) -> torch.Tensor:
+    """Flat FP32 weights of M = 1 (layer 1 hop 0 -> hidden channel 0 and layer 2
+    hidden channel 0 -> output are the spin identity, all else 0) plus real and
+    imaginary Gaussian noise of the given scale (seeded, numpy PCG64)."""
+    import numpy as np
+    per_layer = 9 * c_mid * 16 * 2
+    w = np.random.default_rng(seed).normal(0.0, scale, 2 * per_layer)
+    w1 = w[:per_layer].reshape(9, c_mid, 4, 4, 2)
+    w2 = w[per_layer:].reshape(9, c_mid, 4, 4, 2)
+    for s in range(4):
+        w1[0, 0, s, s, 0] += 1.0
+        w2[0, 0, s, s, 0] += 1.0
+    return torch.from_numpy(w).to(torch.float32)

@@ -1,0 +1,125 @@
+"""Measurements beside the headline solve: batched right-hand sides and the
+learned preconditioner, run through the C ABI on synthetic workloads.
+
+* ``batched``: the 12 spin-colour point sources at site 0 of a 24^3 x 48
+  lattice solved in one wd_solve_batch call against 12 single solves, and an
+  uneven batch (8^4, 16^3 x 32 and 24^3 x 48, four Gaussian sources each)
+  against the same solves one at a time.
+* ``learned``: M trained on 16^3 x 32 smeared-link configurations (four
+  gauge seeds, pairs (v, A^{-1} v) from the library's float64 solver) and
+  applied as right preconditioner of the FP16 inner solve on a larger lattice,
+  against the unpreconditioned FP16-mixed solve of the same system.
+
+Every step runs in the library's kernels; this module only sequences calls
+and times them with CUDA events on the launching stream.
+"""
+
+from __future__ import annotations
+
+import time
+
+import torch
+
+from . import learned, synth, wd, workloads
+
+SMEARED_SEED = workloads.GAUGE_SEED
+
+
+def _lattice(dims, kappa, seed):
+    u = synth.gauge_smeared(dims, seed=seed)
+    lat = wd.Lattice(dims, kappa)
+    lat.set_gauge(torch.view_as_real(u).contiguous())
+    return lat
+
+
+def _timed(fn, stream):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def _summary(stats):
+    return {"inner_matvecs": sum(s.inner_matvecs for s in stats),
+            "max_true_residual": max(s.true_residual for s in stats),
+            "ok": all(s.status == wd.WD_OK for s in stats)}
+
+
+def batched(kappa: float, tol: float = 1e-10, stream=None) -> dict:
+    stream = stream or torch.cuda.current_stream()
+    res = {}
+    d24 = (24, 24, 24, 48)
+    lat24 = _lattice(d24, kappa, SMEARED_SEED + 1)
+    b = torch.stack([synth.to_host_layout(synth.point_source(d24, s, c)) for s in range(4) for c in range(3)]).cuda()
+    x = torch.zeros_like(b)
+    wd.solve_batch([lat24], [b], [x], tol, "mixed_fp16", stream=stream)        # workspaces and graphs
+    st_b, t_b = _timed(lambda: wd.solve_batch([lat24], [b], [x.zero_()], tol, "mixed_fp16", stream=stream), stream)
+    lat24.solve(b[0], x[0], tol, "mixed_fp16", stream=stream)
+    st_s, t_s = _timed(lambda: [lat24.solve(b[i], x[i].zero_(), tol, "mixed_fp16", stream=stream)
+                                for i in range(b.shape[0])], stream)
+    res["point_sources_24x24x24x48"] = {
+        "nrhs": int(b.shape[0]), "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+        "batched": _summary(st_b), "sequential": _summary(st_s)}
+    del b, x
+    torch.cuda.empty_cache()
+
+    lats = [_lattice((8, 8, 8, 8), kappa, SMEARED_SEED + 3), _lattice((16, 16, 16, 32), kappa, SMEARED_SEED), lat24]
+    bs = [torch.stack([synth.to_host_layout(synth.gaussian_source(l.dims, seed=900 + 10 * i + j)) for j in range(4)]).cuda()
+          for i, l in enumerate(lats)]
+    xs = [torch.zeros_like(v) for v in bs]
+    wd.solve_batch(lats, bs, xs, tol, "mixed_fp16", stream=stream)
+    st_b, t_b = _timed(lambda: wd.solve_batch(lats, bs, [v.zero_() for v in xs], tol, "mixed_fp16", stream=stream),
+                       stream)
+
+    def one_by_one():
+        out = []
+        for l, bb, xx in zip(lats, bs, xs):
+            for j in range(bb.shape[0]):
+                out.append(l.solve(bb[j], xx[j].zero_(), tol, "mixed_fp16", stream=stream))
+        return out
+    one_by_one()
+    st_s, t_s = _timed(one_by_one, stream)
+    res["uneven_8x8x8x8_16x16x16x32_24x24x24x48"] = {
+        "nrhs": 12, "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+        "batched": _summary(st_b), "sequential": _summary(st_s)}
+    for l in lats:
+        l.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def learned_preconditioner(kappa: float, test_lat: "wd.Lattice", b: torch.Tensor, tol: float = 1e-10, stream=None,
+                           configs: int = 4, samples: int = 8, steps: int = 60, lr: float = 3e-3, mu: float = 1.0,
+                           seed: int = 11) -> dict:
+    stream = stream or torch.cuda.current_stream()
+    w = learned.initial_weights(seed)
+    t0 = time.perf_counter()
+    losses = []
+    for c in range(configs):
+        lat = _lattice((16, 16, 16, 32), kappa, SMEARED_SEED + 100 + c)
+        v, y = learned.make_samples(lat, samples, seed=2000 + 100 * c)
+        lat.precond_set(w)
+        losses += learned.train(lat, v, y, steps=steps, lr=lr, mu=mu, batch=4)
+        w = lat.precond_get()
+        lat.close()
+        del v, y
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    test_lat.precond_set(w)
+    x = torch.zeros_like(b)
+    test_lat.solve(b, x, tol, "mixed_fp16_learned", stream=stream)
+    st_l, t_l = _timed(lambda: test_lat.solve(b, x.zero_(), tol, "mixed_fp16_learned", stream=stream), stream)
+    st_p, t_p = _timed(lambda: test_lat.solve(b, x.zero_(), tol, "mixed_fp16", stream=stream), stream)
+    return {
+        "train": {"lattice": [16, 16, 16, 32], "configs": configs, "samples_per_config": samples,
+                  "adam_steps": steps * configs, "lr": lr, "mu": mu, "first_loss": losses[0],
+                  "last_loss": losses[-1], "seconds": train_s},
+        "learned": {"time_s": t_l, "inner_matvecs": st_l.inner_matvecs, "outer_iterations": st_l.outer_iterations,
+                    "true_residual": st_l.true_residual, "status": st_l.status},
+        "plain": {"time_s": t_p, "inner_matvecs": st_p.inner_matvecs, "outer_iterations": st_p.outer_iterations,
+                  "true_residual": st_p.true_residual, "status": st_p.status},
+        "matvec_ratio": st_l.inner_matvecs / max(1, st_p.inner_matvecs), "time_ratio": t_l / t_p,
+    }

@@ -24,7 +24,7 @@ GAUGE_SEED = 20260214
 SOURCE_SEED = 450
 # Smallest kappa of each calibration grid in the 500-1500 iteration window
 # (tests/golden/kappa_calibration_<lattice>.txt, written by oracle/calibrate_kappa.py).
-KAPPA = {"16x16x16x32": 0.1265, "32x32x32x64": None}
+KAPPA = {"16x16x16x32": 0.1265, "32x32x32x64": 0.1255}
 
 
 @dataclass(frozen=True)
