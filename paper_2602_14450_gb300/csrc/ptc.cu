@@ -17,6 +17,7 @@
 // Training kernels compute, for L = sum |M v - y|^2/|y|^2 + mu |A M v - v|^2/|v|^2,
 // the weight gradients dL/dRe W + i dL/dIm W by the adjoint network.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -289,7 +290,9 @@ __global__ void __launch_bounds__(128) k_ptc_s1(Geom g, const uint4* in_e, uint4
 }
 
 // Second pass on the even sites x: M psi(x) = V[0][0] psi(x) + sum_d T_{1+d} phi_{1+d}(x).
-template <typename TIN, typename TPHI, typename TOUT, typename LT, int R>
+// CMAJOR: phi units are colour-major (unit a = spins 0..3 of colour a, as the
+// tensor-core first pass writes them); otherwise the spinor order of load_spinor.
+template <typename TIN, typename TPHI, typename TOUT, typename LT, int R, bool CMAJOR>
 __global__ void __launch_bounds__(128) k_ptc_s2(Geom g, const uint4* in_e, const uint4* phi, long long pvs,
                                                 uint4* out_e, const uint4* links_e, const float2* V,
                                                 const SolverState* guard) {
@@ -309,7 +312,18 @@ __global__ void __launch_bounds__(128) k_ptc_s2(Geom g, const uint4* in_e, const
             bool wrap;
             const int hn = neighbour(g, h, co, d, &wrap);
             float m[18], t[24];
-            load_spinor<TPHI>(phi + (size_t)d * pvs, g.Vh, hn, f);
+            if constexpr (CMAJOR) {
+                constexpr int NU = Unit<TPHI>::N;
+                static_assert(NU == 8, "colour-major phi holds 8 reals per unit");
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const uint4 w = __ldg(phi + (size_t)d * pvs + (size_t)a * g.Vh + hn);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f[2 * (3 * (e >> 1) + a) + (e & 1)] = Unit<TPHI>::get(w, e);
+                }
+            } else {
+                load_spinor<TPHI>(phi + (size_t)d * pvs, g.Vh, hn, f);
+            }
             load_link<LT, R>(links_e, g.Vh, h, d, m);
             colour_mul(m, f, t);
             const float ph = (wrap && g.bc[d >> 1] < 0) ? -1.f : 1.f;
@@ -319,6 +333,12 @@ __global__ void __launch_bounds__(128) k_ptc_s2(Geom g, const uint4* in_e, const
         store_spinor<TOUT>(out_e, g.Vh, h, acc);
     }
 }
+
+}  // namespace wd
+
+#include "ptc_tc.cuh"
+
+namespace wd {
 
 // Weight gradient: dW[k][c] += sum_x sum_colour G_c(x) (x) conj(T_k F_c(x)), summed into
 // grad (float, [k][c][s][t][re,im]). Mode 0 (layer 2): G = one even channel,
@@ -495,6 +515,9 @@ cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_
     return cudaGetLastError();
 }
 
+// Device flag raised by a kernel whose bounded wait gave up.
+int* ptc_err(wd_handle* h) { return (int*)workspace(h, "ptc.err", sizeof(int)); }
+
 // Intermediate fields phi_{1+d} of the collapsed M: 8 odd-site vectors in the
 // storage type of `prec` (FP32 for WD_FP32, BF16 otherwise).
 static uint4* ptc_phi(wd_handle* h, int prec) {
@@ -504,8 +527,18 @@ static uint4* ptc_phi(wd_handle* h, int prec) {
 
 // out = M in through the collapsed form: FP32 path (FP32 fields, FP32 18-real
 // links) or FP16 path (FP16 in/out, BF16 phi, FP16 12-real links).
+// Whether the FP16 path mixes on the tensor cores (environment WD_PTC_TC=0 selects the FP32-core pass).
+static bool ptc_tensor_cores() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("WD_PTC_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* PHI, const float2* V,
-                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard) {
+                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard, int* err) {
     const Geom& g = h->g;
     long long groups = ((long long)g.Vh + S1_SITES - 1) / S1_SITES;
     const long long cap = (long long)num_sms() * 6;
@@ -514,11 +547,27 @@ cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e,
     if (prec == WD_FP32) {
         const long long pvs = (long long)spinor_units(WD_FP32) * g.Vh;
         k_ptc_s1<float, float, float, 18><<<g1, 128, 0, s>>>(g, in_e, PHI, pvs, lo, V, guard);
-        k_ptc_s2<float, float, float, float, 18><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
+        k_ptc_s2<float, float, float, float, 18, false><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
+    } else if (ptc_tensor_cores()) {
+        const long long pvs = (long long)spinor_units(WD_BF16) * g.Vh;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_ptc_s1_tc<__half, __half, 12>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const long long tiles = ((long long)g.Vh + tc::TILE_M - 1) / tc::TILE_M;
+        const long long tcap = (long long)num_sms() * 3;
+        const int gt = (int)(tiles < tcap ? tiles : tcap);
+        k_ptc_s1_tc<__half, __half, 12><<<gt, 128, tc::SMEM_BYTES, s>>>(g, in_e, PHI, pvs, lo, V, guard, err);
+        k_ptc_s2<__half, __nv_bfloat16, __half, __half, 12, true><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V,
+                                                                                       guard);
     } else {
         const long long pvs = (long long)spinor_units(WD_BF16) * g.Vh;
         k_ptc_s1<__half, __nv_bfloat16, __half, 12><<<g1, 128, 0, s>>>(g, in_e, PHI, pvs, lo, V, guard);
-        k_ptc_s2<__half, __nv_bfloat16, __half, __half, 12><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
+        k_ptc_s2<__half, __nv_bfloat16, __half, __half, 12, false><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V,
+                                                                                        guard);
     }
     return cudaGetLastError();
 }
@@ -661,8 +710,15 @@ extern "C" int wd_precond_apply(wd_handle* h, int prec, const void* in, void* ou
     const uint4 *le, *lo;
     if ((rc = ensure_links(h, prec, prec == WD_FP32 ? 18 : 12, &le, &lo)) != WD_OK) return rc;
     uint4* PHI = ptc_phi(h, prec);
-    if (!PHI) return fail(h, WD_ERR_CUDA, "out of device memory");
-    WD_CUDA(h, ptc_apply_m(h, prec, (const uint4*)in, (uint4*)out, PHI, B.V, le, lo, (cudaStream_t)stream, nullptr));
+    int* err = ptc_err(h);
+    if (!PHI || !err) return fail(h, WD_ERR_CUDA, "out of device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    WD_CUDA(h, cudaMemsetAsync(err, 0, sizeof(int), s));
+    WD_CUDA(h, ptc_apply_m(h, prec, (const uint4*)in, (uint4*)out, PHI, B.V, le, lo, s, nullptr, err));
+    int herr = 0;
+    WD_CUDA(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WD_CUDA(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, WD_ERR_TIMEOUT, "wd_precond_apply: a bounded tensor-core wait gave up");
     return WD_OK;
 }
 

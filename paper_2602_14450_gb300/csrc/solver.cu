@@ -30,7 +30,8 @@ struct SchemeCfg {
 };
 
 cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* PHI, const float2* V,
-                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard);
+                        const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard, int* err);
+int* ptc_err(wd_handle* h);
 const float2* ptc_collapsed(wd_handle* h);
 uint4* ptc_phi16(wd_handle* h);
 
@@ -69,6 +70,7 @@ struct Sys {
     uint4 *r, *rs, *p, *v, *t, *xt, *tmp;                              // inner precision, nrhs each
     uint4 *phat = nullptr, *shat = nullptr, *PHI = nullptr;            // M p, M s, fields of the collapsed M
     const float2* V = nullptr;                                         // collapsed preconditioner weights
+    int* err = nullptr;                                                // raised by a bounded wait that gave up
     std::vector<double> eta_norm;
     std::vector<bool> active;
 };
@@ -104,7 +106,10 @@ static int prepare(Sys& S, int prec, int recon_lo, bool learned) {
         S.shat = (uint4*)workspace(h, pre + "shat", blo);
         S.PHI = ptc_phi16(h);
         S.V = ptc_collapsed(h);
-        if (!S.phat || !S.shat || !S.PHI || !S.V) return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
+        S.err = ptc_err(h);
+        if (!S.phat || !S.shat || !S.PHI || !S.V || !S.err)
+            return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
+        if (cudaMemset(S.err, 0, sizeof(int)) != cudaSuccess) return fail(h, WD_ERR_CUDA, "cudaMemset");
     }
     const size_t lexb = (size_t)S.nrhs * 2 * h->g.Vh * 24 * sizeof(double);
     S.bl = const_cast<double*>(S.b);
@@ -167,7 +172,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         if ((e = Ops<T>::pupdate(n, nr, vs, S.p, S.v, S.r, st, s)) != cudaSuccess) return e;
         const uint4* pa = S.p;   // operand of A
         if (learned) {
-            if ((e = ptc_apply_m(h, WD_FP16, S.p, S.phat, S.PHI, S.V, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            if ((e = ptc_apply_m(h, WD_FP16, S.p, S.phat, S.PHI, S.V, S.le, S.lo, s, st, S.err)) != cudaSuccess) return e;
             pa = S.phat;
         }
         // v = A p = p - kappa^2 H_eo H_oe p ; alpha = rho / (r*, v)
@@ -180,7 +185,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         if ((e = Ops<T>::supdate(n, nr, vs, S.r, S.v, st, s)) != cudaSuccess) return e;
         const uint4* sa = S.r;   // operand of A
         if (learned) {
-            if ((e = ptc_apply_m(h, WD_FP16, S.r, S.shat, S.PHI, S.V, S.le, S.lo, s, st)) != cudaSuccess) return e;
+            if ((e = ptc_apply_m(h, WD_FP16, S.r, S.shat, S.PHI, S.V, S.le, S.lo, s, st, S.err)) != cudaSuccess) return e;
             sa = S.shat;
         }
         // t = A s ; omega from (t, s), (t, t), (s, s)
@@ -471,6 +476,13 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
     }
     WD_CUDA(h0, cudaEventRecord(h0->t1, s));
     if ((rc = read_states(sys, s)) != WD_OK) return rc;
+    bool timed_out = false;   // a bounded device wait of the preconditioner gave up
+    for (auto& S : sys) {
+        if (!S.err) continue;
+        int herr = 0;
+        WD_CUDA(S.h, cudaMemcpy(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost));
+        timed_out = timed_out || herr != 0;
+    }
     float ms = 0;
     cudaEventElapsedTime(&ms, h0->t0, h0->t1);
     int worst = WD_OK;
@@ -484,6 +496,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             o.true_residual = en > 0 ? std::sqrt(S.h->hst[r].acc) / en : 0.0;
             if (o.outer_iterations == 0) o.first_inner_nonzeros = -1;
             int st = status[k];
+            if (timed_out) st = WD_ERR_TIMEOUT;
             if (st == WD_OK && !(o.true_residual <= tol))
                 st = std::isfinite(o.true_residual) ? WD_ERR_NOT_CONVERGED : WD_ERR_NONFINITE;
             o.status = st;

@@ -108,3 +108,25 @@ def test_learned_scheme_needs_weights():
     with pytest.raises(wd.WDError) as e:
         lat.solve(b, x, 1e-10, "mixed_fp16_learned")
     assert e.value.code == wd.WD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (8, 8, 8, 8)])
+def test_collapsed_fp16_path_ragged_tiles(dims):
+    """The FP16 path (tensor-core first pass, 128-site tiles) on lattices whose
+    odd-site count is not a multiple of 128 (288 sites: two full tiles and a
+    ragged one) and on several full tiles, against the oracle's layered network
+    and against the FP32 path."""
+    u = synth.gauge_random(dims, 0.5, seed=91)
+    lat = lattice(u, KAPPA, dims)
+    flat, (w1, w2) = bf16_weights(seed=17, scale=0.3)
+    lat.precond_set(flat)
+    psi = W.restrict(synth.gaussian_source(dims, seed=92), 0)
+    want = ptc.apply(u, w1, w2, psi, BC)
+    outs = {}
+    for prec in ("fp16", "fp32"):
+        out = torch.empty(lat.vector_bytes(prec), dtype=torch.uint8, device="cuda")
+        lat.precond_apply(prec, packed_even(lat, prec, psi), out)
+        outs[prec] = unpacked_even(lat, prec, out, dims)
+    assert rel_l2(outs["fp32"], want) <= 2e-6
+    assert rel_l2(outs["fp16"], want) <= 1.5e-2
+    assert rel_l2(outs["fp16"], outs["fp32"]) <= 1.5e-2
