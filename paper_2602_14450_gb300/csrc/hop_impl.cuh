@@ -417,32 +417,6 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Neighbour sites of output site h on parity p; returns the mask of the
-// directions d whose hop wraps around the lattice.
-__device__ __forceinline__ unsigned site_neighbours(const Geom& g, int p, int h, int (&nbr)[8]) {
-    const int Lxh = g.Lxh, Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
-    const int row = g.fxh.div(h);
-    const int xh = h - row * Lxh;
-    const int r2 = g.fy.div(row);
-    const int y = row - r2 * Ly;
-    const int t = g.fz.div(r2);
-    const int z = r2 - t * Lz;
-    const int x = 2 * xh + ((p + y + z + t) & 1);
-    const int sy = Lxh, sz = Lxh * Ly, st = Lxh * Ly * Lz;
-    const bool w0 = x == g.L[0] - 1, w1 = x == 0, w2 = y == Ly - 1, w3 = y == 0;
-    const bool w4 = z == Lz - 1, w5 = z == 0, w6 = t == Lt - 1, w7 = t == 0;
-    nbr[0] = row * Lxh + ((w0 ? 0 : x + 1) >> 1);
-    nbr[1] = row * Lxh + ((w1 ? g.L[0] - 1 : x - 1) >> 1);
-    nbr[2] = w2 ? h - (Ly - 1) * sy : h + sy;
-    nbr[3] = w3 ? h + (Ly - 1) * sy : h - sy;
-    nbr[4] = w4 ? h - (Lz - 1) * sz : h + sz;
-    nbr[5] = w5 ? h + (Lz - 1) * sz : h - sz;
-    nbr[6] = w6 ? h - (Lt - 1) * st : h + st;
-    nbr[7] = w7 ? h + (Lt - 1) * st : h - st;
-    return (unsigned)w0 | (unsigned)w1 << 1 | (unsigned)w2 << 2 | (unsigned)w3 << 3 | (unsigned)w4 << 4 |
-           (unsigned)w5 << 5 | (unsigned)w6 << 6 | (unsigned)w7 << 7;
-}
-
 // Whether unit u (N reals) of a neighbour spinor enters the hop in direction
 // d: the t hops project onto two spin components only (+t: spins 2, 3;
 // -t: spins 0, 1), so a unit holding none of those reals is not copied.

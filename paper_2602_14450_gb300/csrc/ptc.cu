@@ -289,6 +289,84 @@ __global__ void __launch_bounds__(128) k_ptc_s1(Geom g, const uint4* in_e, uint4
     }
 }
 
+// The 2 units of gathered-link storage that hold link d of a site (12 halves
+// of an FP16 12-real link start at element 12 d), and the link rebuilt from them.
+template <typename LT> __device__ __forceinline__ void load_link_units(const uint4* __restrict__ links, int Vh, int h,
+                                                                       int d, uint4 (&u)[2]) {
+    const int base = (12 * d) / Unit<LT>::N;
+    u[0] = __ldg(links + (size_t)base * Vh + h);
+    u[1] = __ldg(links + (size_t)(base + 1) * Vh + h);
+}
+template <typename LT> __device__ __forceinline__ void link_from_units(const uint4 (&u)[2], int d, float (&m)[18]) {
+    constexpr int N = Unit<LT>::N;
+    const int base = (12 * d) / N;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+        const int el = 12 * d + e;
+        m[e] = (float)Unit<LT>::get(u[el / N - base], el % N);
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {   // row 2 = conj(row 0 x row 1)
+        const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+        float re = m[2 * b2 + 1] * m[6 + 2 * b1 + 1];
+        re = __fmaf_rn(-m[2 * b2], m[6 + 2 * b1], re);
+        re = __fmaf_rn(-m[2 * b1 + 1], m[6 + 2 * b2 + 1], re);
+        re = __fmaf_rn(m[2 * b1], m[6 + 2 * b2], re);
+        float nim = m[2 * b2] * m[6 + 2 * b1 + 1];
+        nim = __fmaf_rn(m[2 * b2 + 1], m[6 + 2 * b1], nim);
+        nim = __fmaf_rn(-m[2 * b1], m[6 + 2 * b2 + 1], nim);
+        nim = __fmaf_rn(-m[2 * b1 + 1], m[6 + 2 * b2], nim);
+        m[12 + 2 * b] = re;
+        m[12 + 2 * b + 1] = nim;
+    }
+}
+
+// Second pass of the FP16 path with colour-major phi (as the tensor-core first
+// pass writes it): every direction's phi units and link units are loaded one
+// direction ahead of the arithmetic that uses them.
+template <typename TIN, typename TPHI, typename TOUT, typename LT>
+__global__ void __launch_bounds__(128, 5) k_ptc_s2_pf(Geom g, const uint4* in_e, const uint4* phi, long long pvs,
+                                                      uint4* out_e, const uint4* links_e, const float2* V,
+                                                      const SolverState* guard) {
+    if (guarded(guard, GUARD_INNER)) return;
+    __shared__ float2 v00[16];
+    if (threadIdx.x < 16) v00[threadIdx.x] = V[threadIdx.x];
+    __syncthreads();
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+        int nbr[8];
+        const unsigned wm = site_neighbours(g, 0, h, nbr);
+        uint4 fu[2][3], lu[2][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fu[0][a] = __ldg(phi + (size_t)a * g.Vh + nbr[0]);
+        load_link_units<LT>(links_e, g.Vh, h, 0, lu[0]);
+        float acc[24], f[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+        load_spinor<TIN>(in_e, g.Vh, h, f);
+        spin_mul_add(v00, f, acc);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            if (d + 1 < 8) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    fu[(d + 1) & 1][a] = __ldg(phi + (size_t)(d + 1) * pvs + (size_t)a * g.Vh + nbr[d + 1]);
+                load_link_units<LT>(links_e, g.Vh, h, d + 1, lu[(d + 1) & 1]);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f[2 * (3 * (e >> 1) + a) + (e & 1)] = Unit<TPHI>::get(fu[d & 1][a], e);
+            float m[18], t[24];
+            link_from_units<LT>(lu[d & 1], d, m);
+            colour_mul(m, f, t);
+            const float ph = (((wm >> d) & 1u) && g.bc[d >> 1] < 0) ? -1.f : 1.f;
+#pragma unroll
+            for (int i = 0; i < 24; ++i) acc[i] = __fmaf_rn(ph, t[i], acc[i]);
+        }
+        store_spinor<TOUT>(out_e, g.Vh, h, acc);
+    }
+}
+
 // Second pass on the even sites x: M psi(x) = V[0][0] psi(x) + sum_d T_{1+d} phi_{1+d}(x).
 // CMAJOR: phi units are colour-major (unit a = spins 0..3 of colour a, as the
 // tensor-core first pass writes them); otherwise the spinor order of load_spinor.
@@ -561,8 +639,7 @@ cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e,
         const long long tcap = (long long)num_sms() * 3;
         const int gt = (int)(tiles < tcap ? tiles : tcap);
         k_ptc_s1_tc<__half, __half, 12><<<gt, 128, tc::SMEM_BYTES, s>>>(g, in_e, PHI, pvs, lo, V, guard, err);
-        k_ptc_s2<__half, __nv_bfloat16, __half, __half, 12, true><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V,
-                                                                                       guard);
+        k_ptc_s2_pf<__half, __nv_bfloat16, __half, __half><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
     } else {
         const long long pvs = (long long)spinor_units(WD_BF16) * g.Vh;
         k_ptc_s1<__half, __nv_bfloat16, __half, 12><<<g1, 128, 0, s>>>(g, in_e, PHI, pvs, lo, V, guard);

@@ -164,20 +164,35 @@ __global__ void __launch_bounds__(128, 3) k_ptc_s1_tc(Geom g, const uint4* in_e,
     for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
         const int h = tile * TILE_M + tid;
         const bool ok = h < g.Vh;
-        // transports -> BF16 operand rows (zero rows past the end)
-        Coord co{};
-        if (ok) co = coord_of(g, 1, h);
-#pragma unroll 1
+        static_assert(R == 12 && sizeof(TIN) == 2 && sizeof(LT) == 2, "FP16 input, FP16 12-real links");
+        // transports -> BF16 operand rows (zero rows past the end); each
+        // direction's neighbour and link units are loaded one direction ahead
+        int nbr[8];
+        unsigned wm = 0;
+        uint4 fu[2][3], lu[2][2];
+        if (ok) {
+            wm = site_neighbours(g, 1, h, nbr);
+#pragma unroll
+            for (int u = 0; u < 3; ++u) fu[0][u] = __ldg(in_e + (size_t)u * g.Vh + nbr[0]);
+            load_link_units<LT>(links_o, g.Vh, h, 0, lu[0]);
+        }
+#pragma unroll
         for (int d = 0; d < 8; ++d) {
             float t[24];
             if (ok) {
-                bool wrap;
-                const int hn = neighbour(g, h, co, d, &wrap);
+                if (d + 1 < 8) {
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) fu[(d + 1) & 1][u] = __ldg(in_e + (size_t)u * g.Vh + nbr[d + 1]);
+                    load_link_units<LT>(links_o, g.Vh, h, d + 1, lu[(d + 1) & 1]);
+                }
                 float f[24], m[18];
-                load_spinor<TIN>(in_e, g.Vh, hn, f);
-                load_link<LT, R>(links_o, g.Vh, h, d, m);
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) f[8 * u + i] = Unit<TIN>::get(fu[d & 1][u], i);
+                link_from_units<LT>(lu[d & 1], d, m);
                 colour_mul(m, f, t);
-                if (wrap && g.bc[d >> 1] < 0) {
+                if (((wm >> d) & 1u) && g.bc[d >> 1] < 0) {
 #pragma unroll
                     for (int i = 0; i < 24; ++i) t[i] = -t[i];
                 }

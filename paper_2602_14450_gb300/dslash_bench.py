@@ -1,6 +1,8 @@
-"""Dslash micro-benchmark: the hopping kernel H_eo through wd_apply.
+"""Dslash micro-benchmark: the hopping kernel H_eo through wd_apply, and the
+learned preconditioner M through wd_precond_apply.
 
     python -m paper_2602_14450_gb300.dslash_bench --dims 32,32,32,64 --cases fp16_12,fp32_18 --launches 50
+    python -m paper_2602_14450_gb300.dslash_bench --dims 32,32,32,64 --cases m_fp16 --launches 20
 
 Links are exp(i 0.5 H) random SU(3) matrices generated on the GPU; inputs
 cycle through four different source vectors so that consecutive launches do
@@ -50,6 +52,27 @@ def hop_timing(lat, prec: str, recon: int, launches: int, stream=None) -> dict:
     return {"case": f"{prec}_{recon}", "us": us, "bytes_per_site": bps, "sites": vh, "gbs": bps * vh / (us * 1e-6) / 1e9}
 
 
+def precond_timing(lat, prec: str, launches: int, stream=None) -> dict:
+    """Average time of one application of M (two kernels) on packed even-site vectors."""
+    from . import learned
+    lat.precond_set(learned.initial_weights(3, scale=0.1))
+    vh = lat.vector_bytes(prec) // (24 * BYTES[prec])
+    ins = [torch.randn(vh * 24, dtype=torch.float64, device="cuda").to(
+        {"fp32": torch.float32, "fp16": torch.float16}[prec]).view(torch.uint8) for _ in range(4)]
+    out = torch.empty(lat.vector_bytes(prec), dtype=torch.uint8, device="cuda")
+    stream = stream or torch.cuda.current_stream()
+    for i in range(3):
+        lat.precond_apply(prec, ins[i % 4], out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(launches):
+        lat.precond_apply(prec, ins[i % 4], out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"case": f"m_{prec}", "us": e0.elapsed_time(e1) * 1e3 / launches, "sites": vh}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", default="32,32,32,64")
@@ -66,7 +89,10 @@ def main():
     torch.cuda.empty_cache()
     for c in a.cases.split(","):
         prec, recon = c.split("_")
-        print(json.dumps(hop_timing(lat, prec, int(recon), a.launches)), flush=True)
+        if prec == "m":
+            print(json.dumps(precond_timing(lat, recon, a.launches)), flush=True)
+        else:
+            print(json.dumps(hop_timing(lat, prec, int(recon), a.launches)), flush=True)
 
 
 if __name__ == "__main__":
