@@ -123,3 +123,82 @@ def learned_preconditioner(kappa: float, test_lat: "wd.Lattice", b: torch.Tensor
                   "true_residual": st_p.true_residual, "status": st_p.status},
         "matvec_ratio": st_l.inner_matvecs / max(1, st_p.inner_matvecs), "time_ratio": t_l / t_p,
     }
+
+
+def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 40) -> dict:
+    """The rows of Table 2 on a lattice with the paper's source b = (1, 0, ..., 0)
+    (unit real entry at even site 0, spin 0, colour 0) and its stopping rule
+    |r|^2 < 1e-26 (|b| = 1, so tol = 1e-13): FP64; FP32 inner (s = 1) with
+    eps^2 = 1e-12 and 1e-4; FP16 inner with s = 128, sigma = 64; s = 4096 alone;
+    s = 128, sigma = sigma_lambda = 256 with solution rescaling (Alg. 4); and
+    unrescaled FP16 (Alg. 1), the paper's unimproved case."""
+    stream = stream or torch.cuda.current_stream()
+    b = synth.to_host_layout(synth.point_source(lat.dims, 0, 0, 0)).cuda()
+    x = torch.zeros_like(b)
+    rows = {
+        "double": ("fp64", {}),
+        "fp32_s1_eps2_1e-12": ("mixed_fp32", {"inner_eps": 1e-6}),
+        "fp32_s1_eps2_1e-4": ("mixed_fp32", {}),
+        "fp16_s128_sigma64": ("mixed_fp16", {}),
+        "fp16_s4096": ("mixed_fp16", {"s": 4096.0, "sigma": 0.0}),
+        "fp16_s128_sigma256_lambda256": ("mixed_fp16", {"sigma": 256.0, "sigma_lambda": 256.0, "rescale_x": 1}),
+        "fp16_unrescaled_alg1": ("mixed_fp16_plain", {}),
+    }
+    out = {"source": "b = (1, 0, ..., 0): even site 0, spin 0, colour 0", "tol": tol}
+    for name, (scheme, kw) in rows.items():
+        p = wd.default_params(scheme)
+        p.max_outer = max_outer
+        for k, v in kw.items():
+            setattr(p, k, v)
+        lat.solve(b, x.zero_(), tol, scheme, p, stream=stream, check=False)      # graphs and workspaces
+        st, t = _timed(lambda: lat.solve(b, x.zero_(), tol, scheme, p, stream=stream, check=False), stream)
+        out[name] = {"matvecs": st.inner_matvecs, "outer": st.outer_iterations, "time_s": t, "status": st.status,
+                     "true_residual": st.true_residual, "first_inner_nonzeros": st.first_inner_nonzeros}
+    return out
+
+
+def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 128.0, 1024.0, 4096.0),
+            sigma_values=(0.0, 1.0, 16.0, 64.0, 256.0, 1024.0), max_outer: int = 30, source: str = "point") -> dict:
+    """FP16 low-precision matvecs to 1e-10 over the Alg. 2 scale s and the Alg. 3
+    residual norm sigma (sigma = 0: no inner rescaling), recalculated gamma, on
+    the 16^3 x 32 workload with the paper's unit source (or the Gaussian one)
+    -- the counts Sec. 5 plots in its parameter study --
+    plus the four corners of recalculated gamma on/off and solution rescaling
+    (Alg. 4, sigma_lambda = sigma) on/off at s = 128, sigma = 64, and Alg. 1
+    with unrescaled FP16 (the paper's unimproved case). Inner solves stop at 2000
+    matvecs and the refinement at max_outer trips; runs that stop at the caps
+    report their status and the matvecs spent."""
+    stream = stream or torch.cuda.current_stream()
+    dims = (16, 16, 16, 32)
+    lat = _lattice(dims, kappa, SMEARED_SEED)
+    if source == "point":
+        b = synth.to_host_layout(synth.point_source(dims, 0, 0, 0)).cuda()
+    else:
+        b = synth.to_host_layout(synth.gaussian_source(dims, seed=workloads.SOURCE_SEED)).cuda()
+    x = torch.zeros_like(b)
+
+    def run(scheme, **kw):
+        p = wd.default_params(scheme)
+        p.max_outer = max_outer
+        if scheme != "fp64":
+            p.max_inner = 2000          # bounds the work of settings that crawl
+        for k, v in kw.items():
+            setattr(p, k, v)
+        st = lat.solve(b, x.zero_(), tol, scheme, p, stream=stream, check=False)
+        return {"matvecs": st.inner_matvecs, "outer": st.outer_iterations, "status": st.status,
+                "true_residual": st.true_residual}
+
+    grid = {}
+    for s in s_values:
+        for sg in sigma_values:
+            grid[f"s={s:g},sigma={sg:g}"] = run("mixed_fp16", s=s, sigma=sg, sigma_lambda=sg if sg > 0 else 64.0)
+    corners = {}
+    for recalc in (0, 1):
+        for lam in (0, 1):
+            corners[f"recalc_gamma={recalc},rescale_x={lam}"] = run("mixed_fp16", recalc_gamma=recalc, rescale_x=lam)
+    out = {"lattice": list(dims), "kappa": kappa, "source": source, "grid": grid, "corners": corners,
+           "fp16_unrescaled_alg1": run("mixed_fp16_plain"),
+           "fp32_alg1_eps2_1e-4": run("mixed_fp32"),
+           "fp64": run("fp64")}
+    lat.close()
+    return out
