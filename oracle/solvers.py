@@ -160,6 +160,7 @@ class InnerTrace:
     matvecs: int = 0
     iterations: int = 0
     converged: bool = False
+    breakdown: bool = False                         # (r*, v) = 0, (t, t) = 0 or rho' omega' = 0
     first_beta: complex | None = None
     residuals: list = field(default_factory=list)   # |r|/gamma' at each loop test
     iterates: list = field(default_factory=list)    # true solution estimate after each iteration
@@ -199,20 +200,26 @@ def bicgstab_rescaled(apply_a_low, b: torch.Tensor, prm: InnerParams, store=None
             tr.first_beta = beta
         p = store(beta * (p - omega_p * v) + r)
         v = apply_a_low(p)
-        alpha = rho / dot(rstar, v)
+        rv = dot(rstar, v)
+        if rv == 0:                         # breakdown: alpha undefined; stop with the current x
+            tr.breakdown = True
+            break
+        alpha = rho / rv
         r = store(r - alpha * v)
         t = apply_a_low(r)
-        tr.matvecs += 2
         ts, tt, rr = dot(t, r), dot(t, t).real, dot(r, r).real
+        if tt == 0:                         # breakdown: omega undefined
+            tr.breakdown = True
+            break
         omega = ts / tt
-        omega_hat = abs(ts) / math.sqrt(tt * rr)
-        if omega_hat < prm.omega0:
+        omega_hat = abs(ts) / math.sqrt(tt * rr) if rr > 0 else math.inf
+        if 0 < omega_hat < prm.omega0:      # omega_0 prescription (Sec. 3); omega = 0 stays 0
             omega = omega * prm.omega0 / omega_hat
         x = store(x + (lam_p / gamma_p) * (omega * r + alpha * p))
         r = store(r - omega * t)
         if prm.sigma is not None:
             g = norm(r)
-            gamma = prm.sigma / g
+            gamma = prm.sigma / g if g > 0 else math.inf    # r = 0: non-finite, as on the device
             r = store(gamma * r)
             if prm.recalc_gamma:
                 gamma = norm(r) / g          # applied factor: stored norm over g
@@ -223,10 +230,17 @@ def bicgstab_rescaled(apply_a_low, b: torch.Tensor, prm: InnerParams, store=None
         omega_p, alpha_p, rho_p = omega, alpha, gamma * rho
         gamma_p *= gamma
         if prm.rescale_x:
-            lam = sig_l / norm(x)
+            xn = norm(x)
+            lam = sig_l / xn if xn > 0 else math.inf
             x = store(lam * x)
             lam_p *= lam
         tr.iterations += 1
+        tr.matvecs += 2                     # matvecs of completed iterations (two each)
+        if rho_p * omega_p == 0:            # breakdown: the next beta is undefined
+            tr.breakdown = True
+            if keep_iterates:
+                tr.iterates.append(x / lam_p)
+            break
         if keep_iterates:
             tr.iterates.append(x / lam_p)
     return x / lam_p, tr

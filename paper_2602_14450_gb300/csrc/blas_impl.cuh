@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_pupdate(int n, int nrhs, long long vs, 
                 o[2 * i + 1] = b;
             }
         }
-        store_spinor<T>(p, n, h, o);
+        store_spinor<T>(p, n, h, o, st->ftz);
     }
 }
 
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, 
         load_spinor<T>(v, n, h, vv);
 #pragma unroll
         for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], ar, ai, vv[2 * i], vv[2 * i + 1]);
-        store_spinor<T>(r, n, h, rr);
+        store_spinor<T>(r, n, h, rr, st->ftz);
     }
 }
 
@@ -112,12 +112,12 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
             cscale_add(xx[2 * i], xx[2 * i + 1], xr_r, xr_i, rr[2 * i], rr[2 * i + 1]);
             cscale_add(xx[2 * i], xx[2 * i + 1], xp_r, xp_i, pp[2 * i], pp[2 * i + 1]);
         }
-        store_spinor<T>(x, n, h, xx);
+        store_spinor<T>(x, n, h, xx, st->ftz);
         if (xr_src) load_spinor<T>(r, n, h, rr);
         load_spinor<T>(t, n, h, tt);
 #pragma unroll
         for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, tt[2 * i], tt[2 * i + 1]);
-        store_spinor<T>(r, n, h, rr);
+        store_spinor<T>(r, n, h, rr, st->ftz);
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
             s_r2 += rr[i] * rr[i];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, ui
         load_spinor<T>(r, n, h, rr);
 #pragma unroll
         for (int i = 0; i < 24; ++i) rr[i] *= gs;
-        store_spinor<T>(r, n, h, rr);
+        store_spinor<T>(r, n, h, rr, st->ftz);
         load_spinor<T>(rstar, n, h, rs);
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, ui
             load_spinor<T>(x, n, h, xx);
 #pragma unroll
             for (int i = 0; i < 24; ++i) xx[i] *= lam;
-            store_spinor<T>(x, n, h, xx);
+            store_spinor<T>(x, n, h, xx, st->ftz);
         }
     }
     double v[3] = {(double)s_r2, (double)s_re, (double)s_im};

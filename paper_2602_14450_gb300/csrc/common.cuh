@@ -21,6 +21,7 @@ template <typename T> struct Unit;
 template <> struct Unit<double> {
     typedef double C;
     static constexpr int N = 2;
+    __device__ __forceinline__ static uint4 flush(const uint4& u) { return u; }   // FP64 storage is not flushed
     __device__ __forceinline__ static C get(const uint4& u, int i) {
         return i == 0 ? __hiloint2double((int)u.y, (int)u.x) : __hiloint2double((int)u.w, (int)u.z);
     }
@@ -37,6 +38,9 @@ template <> struct Unit<double> {
 template <> struct Unit<float> {
     typedef float C;
     static constexpr int N = 4;
+    // Stored subnormals (exponent field 0) become +0.
+    __device__ __forceinline__ static unsigned fw(unsigned w) { return (w & 0x7F800000u) ? w : 0u; }
+    __device__ __forceinline__ static uint4 flush(const uint4& u) { return make_uint4(fw(u.x), fw(u.y), fw(u.z), fw(u.w)); }
     __device__ __forceinline__ static C get(const uint4& u, int i) {
         unsigned w = i == 0 ? u.x : i == 1 ? u.y : i == 2 ? u.z : u.w;
         return __uint_as_float(w);
@@ -50,9 +54,17 @@ __device__ __forceinline__ unsigned word_of(const uint4& u, int w) {
     return w == 0 ? u.x : w == 1 ? u.y : w == 2 ? u.z : u.w;
 }
 
+// Both 16-bit lanes of a word with subnormal values (exponent field 0) set to +0.
+__device__ __forceinline__ unsigned flush16(unsigned w, unsigned emask) {
+    return ((w & emask) ? (w & 0xFFFFu) : 0u) | ((w & (emask << 16)) ? (w & 0xFFFF0000u) : 0u);
+}
+
 template <> struct Unit<__half> {
     typedef float C;
     static constexpr int N = 8;
+    __device__ __forceinline__ static uint4 flush(const uint4& u) {
+        return make_uint4(flush16(u.x, 0x7C00u), flush16(u.y, 0x7C00u), flush16(u.z, 0x7C00u), flush16(u.w, 0x7C00u));
+    }
     __device__ __forceinline__ static C get(const uint4& u, int i) {
         unsigned w = word_of(u, i >> 1);
         __half2 h = *reinterpret_cast<__half2*>(&w);
@@ -73,6 +85,9 @@ template <> struct Unit<__half> {
 template <> struct Unit<__nv_bfloat16> {
     typedef float C;
     static constexpr int N = 8;
+    __device__ __forceinline__ static uint4 flush(const uint4& u) {
+        return make_uint4(flush16(u.x, 0x7F80u), flush16(u.y, 0x7F80u), flush16(u.z, 0x7F80u), flush16(u.w, 0x7F80u));
+    }
     __device__ __forceinline__ static C get(const uint4& u, int i) {
         unsigned w = word_of(u, i >> 1);
         __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
@@ -121,13 +136,16 @@ __device__ __forceinline__ void load_spinor_cg(const uint4* v, int stride, int h
 }
 
 // Round to storage and write; `s` is overwritten with the stored values so
-// that reductions see exactly what later kernels will read.
+// that reductions see exactly what later kernels will read. With ftz, stored
+// subnormal values are flushed to zero after the rounding.
 template <typename T>
-__device__ __forceinline__ void store_spinor(uint4* v, int stride, int h, typename Unit<T>::C (&s)[24]) {
+__device__ __forceinline__ void store_spinor(uint4* v, int stride, int h, typename Unit<T>::C (&s)[24],
+                                             bool ftz = false) {
     constexpr int N = Unit<T>::N;
 #pragma unroll
     for (int u = 0; u < 24 / N; ++u) {
         uint4 w = Unit<T>::put(&s[u * N]);
+        if (ftz) w = Unit<T>::flush(w);
         v[(size_t)u * stride + h] = w;
 #pragma unroll
         for (int i = 0; i < N; ++i) s[u * N + i] = Unit<T>::get(w, i);
@@ -264,6 +282,7 @@ struct SolverState {
     int recalc, rescale_x, max_matvecs, scale_pass;
     int iter, matvecs, first, done, status;
     int skip;                       // right-hand side finished: every kernel leaves it alone
+    int ftz;                        // flush subnormal values of every low-precision store
     // refinement (outer) scalars
     double rnorm;                   // |b^ - A x| of the FP64 outer residual
     double shat;                    // |single(y~)|

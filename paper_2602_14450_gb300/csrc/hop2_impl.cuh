@@ -71,7 +71,7 @@ __device__ __forceinline__ void load_pair(const uint4* __restrict__ v, int strid
 
 // Round pairs to storage and write both sites; s is replaced by the stored values.
 template <typename T>
-__device__ __forceinline__ void store_pair(uint4* v, int stride, int a, int b, float2 (&s)[24]) {
+__device__ __forceinline__ void store_pair(uint4* v, int stride, int a, int b, float2 (&s)[24], bool ftz) {
     constexpr int N = Unit<T>::N;
     typedef typename Unit<T>::C C;
 #pragma unroll
@@ -82,7 +82,11 @@ __device__ __forceinline__ void store_pair(uint4* v, int stride, int a, int b, f
             va[i] = s[u * N + i].x;
             vb[i] = s[u * N + i].y;
         }
-        const uint4 wa = Unit<T>::put(va), wb = Unit<T>::put(vb);
+        uint4 wa = Unit<T>::put(va), wb = Unit<T>::put(vb);
+        if (ftz) {
+            wa = Unit<T>::flush(wa);
+            wb = Unit<T>::flush(wb);
+        }
         v[(size_t)u * stride + a] = wa;
         v[(size_t)u * stride + b] = wb;
 #pragma unroll
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
 #pragma unroll
             for (int i = 0; i < 24; ++i) o[i] = fma2(C2, zv[i], o[i]);
         }
-        store_pair<T>(vout, Vh, ha, hb, o);
+        store_pair<T>(vout, Vh, ha, hb, o, P.guard != nullptr && P.guard[sl.rhs].ftz);
 
         if constexpr (RED == RED_RSV) {
             float2 rs[24];

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) hop3_kernel(const HopParams P, const Stag
 #pragma unroll
                 for (int q = 0; q < 24; ++q) o[q] = fma2(C2, zv[q], o[q]);
             }
-            store_pair<T>(vout, Vh, ha, hb, o);
+            store_pair<T>(vout, Vh, ha, hb, o, P.guard != nullptr && P.guard[sl.rhs].ftz);
             if constexpr (RED == RED_RSV) {
                 float2 rs[24];
                 load_pair<T>(vrs, Vh, ha, hb, rs);

@@ -214,7 +214,7 @@ __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_U
 template <typename T, int EPI, int RED>
 __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, const uint4* vy, const uint4* vz,
                                              const uint4* vrs, int h, typename Unit<T>::C (&acc)[24],
-                                             typename Unit<T>::C (&part)[RedSums<RED>::N]) {
+                                             typename Unit<T>::C (&part)[RedSums<RED>::N], bool ftz) {
     typedef typename Unit<T>::C C;
     constexpr int NS = RedSums<RED>::N;
     const int Vh = P.g.Vh;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, co
 #pragma unroll
         for (int i = 0; i < 24; ++i) o[i] += cc * zv[i];
     }
-    store_spinor<T>(vout, Vh, h, o);
+    store_spinor<T>(vout, Vh, h, o, ftz);
 
     if constexpr (RED == RED_RSV) {
         C rs[24];
@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T)
     constexpr int NS = RedSums<RED>::N;
     const Slice sl = slice_of(P.nrhs);
     if (guarded(P.guard ? P.guard + sl.rhs : nullptr, P.guard_kind)) return;
+    const bool ftz = P.guard != nullptr && P.guard[sl.rhs].ftz;
     const long long ro = (long long)sl.rhs * P.vs;     // this right-hand side's vectors
     const uint4* __restrict__ vin = P.in + ro;
     uint4* vout = P.out + ro;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T)
             }
         }
 
-        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part);
+        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part, ftz);
     }
 
     if constexpr (RED != RED_NONE) {
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(RingFmt<T, R>::BLOCK, 6) hop_ring_kernel(const
     extern __shared__ uint4 ring[];
     const Slice sl = slice_of(P.nrhs);
     if (guarded(P.guard ? P.guard + sl.rhs : nullptr, P.guard_kind)) return;
+    const bool ftz = P.guard != nullptr && P.guard[sl.rhs].ftz;
     const long long ro = (long long)sl.rhs * P.vs;
     const uint4* __restrict__ vin = P.in + ro;
     uint4* vout = P.out + ro;
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(RingFmt<T, R>::BLOCK, 6) hop_ring_kernel(const
                 reconstruct<C>(mu, fwd, f, chi, acc);
             }
         }
-        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part);
+        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part, ftz);
         h = hn;
         wm = wmn;
 #pragma unroll

@@ -390,6 +390,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                     q.recalc = prm.recalc_gamma;
                     q.rescale_x = prm.rescale_x;
                     q.scale_pass = scale_pass ? 1 : 0;
+                    q.ftz = prm.ftz ? 1 : 0;
                     q.max_matvecs = prm.max_inner;
                     // FP64 BiCGStab: one inner solve to the outer tolerance; mixed: eps of Table 2
                     q.eps = cfg.fp64_inner ? std::max(0.5 * tol * en / rn, 1e-15) : prm.inner_eps;

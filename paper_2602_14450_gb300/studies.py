@@ -131,7 +131,9 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
     |r|^2 < 1e-26 (|b| = 1, so tol = 1e-13): FP64; FP32 inner (s = 1) with
     eps^2 = 1e-12 and 1e-4; FP16 inner with s = 128, sigma = 64; s = 4096 alone;
     s = 128, sigma = sigma_lambda = 256 with solution rescaling (Alg. 4); and
-    unrescaled FP16 (Alg. 1), the paper's unimproved case."""
+    unrescaled FP16 (Alg. 1), the paper's unimproved case -- the last and the
+    first FP16 row also with subnormals flushed to zero on every store, the
+    regime of the paper's build."""
     stream = stream or torch.cuda.current_stream()
     b = synth.to_host_layout(synth.point_source(lat.dims, 0, 0, 0)).cuda()
     x = torch.zeros_like(b)
@@ -143,6 +145,9 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
         "fp16_s4096": ("mixed_fp16", {"s": 4096.0, "sigma": 0.0}),
         "fp16_s128_sigma256_lambda256": ("mixed_fp16", {"sigma": 256.0, "sigma_lambda": 256.0, "rescale_x": 1}),
         "fp16_unrescaled_alg1": ("mixed_fp16_plain", {}),
+        # the paper's build flushes subnormals (-Kfz): the same two FP16 forms with every store flushed
+        "fp16_s128_sigma64_ftz": ("mixed_fp16", {"ftz": 1}),
+        "fp16_unrescaled_alg1_ftz": ("mixed_fp16_plain", {"ftz": 1}),
     }
     out = {"source": "b = (1, 0, ..., 0): even site 0, spin 0, colour 0", "tol": tol}
     for name, (scheme, kw) in rows.items():

@@ -149,3 +149,42 @@ def test_storage_rounding_formats():
     assert torch.equal(got, want)
     bf = S._round_bf16(torch.tensor([1 + 2 ** -8, 1 + 3 * 2 ** -8, 2 ** -130, 3.0e38]).numpy())
     assert list(bf) == [1.0, 1 + 2 ** -6, 2 ** -130, float(torch.tensor(3.0e38).to(torch.bfloat16).double())]
+
+
+def test_inner_breakdown_stops_without_raising():
+    """Algorithm 3 breaks down when (r*, v) = 0 (here A = 0): the oracle stops
+    the inner solve with x = 0 and flags it, as the device recurrence does
+    (status breakdown, the refinement continues), instead of dividing by zero."""
+    b = torch.randn(40, dtype=torch.complex128, generator=torch.Generator().manual_seed(3))
+    x, tr = S.bicgstab_rescaled(lambda f: torch.zeros_like(f), b, S.InnerParams(sigma=64.0))
+    assert tr.breakdown and not tr.converged
+    assert tr.iterations == 0 and tr.matvecs == 0
+    assert torch.count_nonzero(x) == 0
+
+
+def test_fp16_flush_to_zero_slows_unrescaled_inner_solve():
+    """Sec. 5: with the paper's unit source and FP16 subnormals flushed to zero
+    (its -Kfz build), the unrescaled inner solve of Alg. 1 loses vector
+    elements to underflow and needs far more matvecs, while Alg. 2 + Alg. 3
+    (s = 128, sigma = 64) keeps its vectors in range and is unaffected. Without
+    the flush the two cost the same. (On 8^3 x 16 the gap is 3804 vs 434.)"""
+    from oracle import wilson as W
+    from paper_2602_14450_gb300 import synth
+    dims = (4, 4, 4, 8)
+    u = synth.gauge_smeared(dims, seed=5)
+    eta = synth.point_source(dims, 0, 0, 0)
+    runs = {}
+    for ftz in (False, True):
+        for name, outer, inner in [
+            ("alg1", S.OuterParams(s=1.0, use_shat=False, tol=1e-13, max_outer=25),
+             S.InnerParams(sigma=None, max_matvecs=600)),
+            ("alg23", S.OuterParams(s=128.0, use_shat=True, tol=1e-13, max_outer=25),
+             S.InnerParams(sigma=64.0, max_matvecs=600)),
+        ]:
+            x, tr = S.solve_wilson_mixed(u, eta, 0.124, fmt="fp16", outer=outer, inner=inner, ftz=ftz)
+            assert tr.converged and S.norm(eta - W.dirac(u, x, 0.124)) / S.norm(eta) <= 1e-13
+            runs[name, ftz] = tr
+    n = 2 * dims[0] * dims[1] * dims[2] * dims[3] // 2 * 12       # reals of an even-site vector
+    assert runs["alg1", False].nonzeros[1] == n and runs["alg1", True].nonzeros[1] < n
+    assert runs["alg1", True].matvecs >= 1.4 * runs["alg1", False].matvecs
+    assert abs(runs["alg23", True].matvecs - runs["alg23", False].matvecs) <= 0.1 * runs["alg23", False].matvecs
