@@ -205,3 +205,27 @@ def test_flush_to_zero_regime_of_the_paper():
     plain_status, plain_ftz = counts["mixed_fp16_plain", 1]
     assert plain_status != wd.WD_OK or plain_ftz >= 3 * counts["mixed_fp16_plain", 0][1], counts
     assert counts["mixed_fp16", 1][1] <= 1.25 * counts["mixed_fp16", 0][1], counts
+
+
+def test_full_size_solution_sampled_residual():
+    """The benchmark solve (32^3 x 64 smeared links, kappa of the workload,
+    Gaussian source; FP16-mixed, FP64 and learned-preconditioned forms) checked
+    by the oracle: eta - D x from Eq. 1 at 3000 sampled sites (both parities)
+    must be as small, relative to eta there, as the tolerance asks."""
+    from paper_2602_14450_gb300 import learned, workloads
+    wl = workloads.get("32x32x32x64")
+    u = wl.gauge()
+    eta = wl.source()
+    lat = lattice(u, wl.kappa, wl.dims)
+    b = lex_dev(eta)
+    g = torch.Generator().manual_seed(1)
+    sites = torch.randint(wl.volume, (3000,), generator=g)
+    eta_s = eta.reshape(-1, 4, 3)[sites]
+    lat.precond_set(learned.initial_weights(5, scale=0.02))
+    for scheme in ("mixed_fp16", "fp64", "mixed_fp16_learned"):
+        x = torch.zeros_like(b)
+        st = lat.solve(b, x, TOL, scheme)
+        assert st.status == wd.WD_OK and st.true_residual <= TOL, (scheme, st.true_residual)
+        xs = from_lex(x, wl.dims)
+        r = eta_s - (xs.reshape(-1, 4, 3)[sites] - wl.kappa * W.hop_at_sites(u, xs, sites, BC))
+        assert S.norm(r) / S.norm(eta_s) <= 3 * TOL, scheme
