@@ -17,7 +17,7 @@ int hop_variant() {
     static int v = 0;
     if (v == 0) {
         const char* e = std::getenv("WD_HOP_KERNEL");
-        v = (e && e[0] >= '1' && e[0] <= '5') ? e[0] - '0' : 4;
+        v = (e && e[0] >= '1' && e[0] <= '6') ? e[0] - '0' : 4;
     }
     return v;
 }

@@ -265,7 +265,65 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, co
     }
 }
 
-template <typename T, int R, int EPI, int RED, bool PF>
+// link_mul with FP32 arithmetic on packed pairs: the two half-spinor columns
+// k = 0, 1 share every link element, so each complex multiply-add of a row is
+// four FP32x2 fused multiply-adds on (column 0, column 1) pairs.
+template <typename T, int R>
+__device__ __forceinline__ void link_mul_pair(const uint4 (&u)[LinkFmt<T, R>::GROUP_UNITS], int off,
+                                              const float (&h)[12], float (&x)[12]) {
+    constexpr int N = Unit<T>::N;
+    float m[18];
+#pragma unroll
+    for (int e = 0; e < R; ++e) m[e] = Unit<T>::get(u[(off + e) / N], (off + e) % N);
+    if (R == 12) {
+#define MR(a, b) m[2 * (3 * (a) + (b))]
+#define MI(a, b) m[2 * (3 * (a) + (b)) + 1]
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+            float re = MI(0, b2) * MI(1, b1);
+            re = __fmaf_rn(-MR(0, b2), MR(1, b1), re);
+            re = __fmaf_rn(-MI(0, b1), MI(1, b2), re);
+            re = __fmaf_rn(MR(0, b1), MR(1, b2), re);
+            float nim = MR(0, b2) * MI(1, b1);
+            nim = __fmaf_rn(MI(0, b2), MR(1, b1), nim);
+            nim = __fmaf_rn(-MR(0, b1), MI(1, b2), nim);
+            nim = __fmaf_rn(-MI(0, b1), MR(1, b2), nim);
+            m[12 + 2 * b] = re;
+            m[12 + 2 * b + 1] = nim;
+        }
+#undef MR
+#undef MI
+    }
+    float2 hr[3], hi[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        hr[b] = make_float2(h[2 * b], h[6 + 2 * b]);
+        hi[b] = make_float2(h[2 * b + 1], h[6 + 2 * b + 1]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float* mr = &m[6 * a];
+        float2 re = __fmul2_rn(make_float2(mr[0], mr[0]), hr[0]);
+        re = __ffma2_rn(make_float2(-mr[1], -mr[1]), hi[0], re);
+        re = __ffma2_rn(make_float2(mr[2], mr[2]), hr[1], re);
+        re = __ffma2_rn(make_float2(-mr[3], -mr[3]), hi[1], re);
+        re = __ffma2_rn(make_float2(mr[4], mr[4]), hr[2], re);
+        re = __ffma2_rn(make_float2(-mr[5], -mr[5]), hi[2], re);
+        float2 im = __fmul2_rn(make_float2(mr[0], mr[0]), hi[0]);
+        im = __ffma2_rn(make_float2(mr[1], mr[1]), hr[0], im);
+        im = __ffma2_rn(make_float2(mr[2], mr[2]), hi[1], im);
+        im = __ffma2_rn(make_float2(mr[3], mr[3]), hr[1], im);
+        im = __ffma2_rn(make_float2(mr[4], mr[4]), hi[2], im);
+        im = __ffma2_rn(make_float2(mr[5], mr[5]), hr[2], im);
+        x[2 * a] = re.x;
+        x[6 + 2 * a] = re.y;
+        x[2 * a + 1] = im.x;
+        x[6 + 2 * a + 1] = im.y;
+    }
+}
+
+template <typename T, int R, int EPI, int RED, bool PF, bool PAIR = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T) == 4 ? 2 : 1) hop_kernel(const HopParams P) {
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
@@ -381,7 +439,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T)
                     load_spinor<T>(vin, Vh, hnb[d], nb);
                     project<C>(mu, fwd, nb, hs);
                 }
-                link_mul<T, R>(lu, j * R, hs, chi);
+                if constexpr (PAIR) {
+                    link_mul_pair<T, R>(lu, j * R, hs, chi);
+                } else {
+                    link_mul<T, R>(lu, j * R, hs, chi);
+                }
                 const C f = (mu == 3 ? C(2) : C(1)) * ((wrap && g.bc[mu] < 0) ? C(-1) : C(1));
                 reconstruct<C>(mu, fwd, f, chi, acc);
             }

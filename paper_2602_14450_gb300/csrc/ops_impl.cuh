@@ -114,6 +114,14 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
+    if constexpr (sizeof(T) == 2) {
+        if (hop_variant() == 6) {   // as 4, with the SU(3) products on FP32x2 column pairs
+            const void* k = (const void*)hop_kernel<T, R, E, D, true, true>;
+            const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
+            hop_kernel<T, R, E, D, true, true><<<nb * nr, block, 0, s>>>(P);
+            return cudaGetLastError();
+        }
+    }
     if (hop_variant() == 4) {   // one site per thread, loads one direction ahead
         const void* k = (const void*)hop_kernel<T, R, E, D, true>;
         const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
