@@ -337,6 +337,7 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     P.vs = 0;
     P.guard = nullptr;
     P.guard_kind = GUARD_NONE;
+    apply_tuning(h, prec, recon, P);
     const double k = h->kappa;
     auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y) {
         P.parity = parity;

@@ -31,6 +31,8 @@ struct HopParams {
     const SolverState* guard;  // per-rhs state consulted by the guard
     int guard_kind;            // GuardKind
     int* err;                  // set to 1 by a kernel whose bounded wait gave up (may be null)
+    int variant;               // kernel variant (hop_variant() numbering); 0 = the process default
+    int block;                 // threads per block; 0 = the process default
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.

@@ -66,12 +66,13 @@ bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
 
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
-    const int block = hop_block();
+    const int block = P.block > 0 ? P.block : hop_block();
+    const int variant = P.variant > 0 ? P.variant : hop_variant();
     const int nr = P.nrhs;
     if constexpr (sizeof(T) == 2) {
         StageGeom sg;
         size_t smem = 0;
-        if (hop_variant() == 3 && stage_geom<T, R>(P.g, &sg, &smem)) {   // shared-memory staged tiles
+        if (variant == 3 && stage_geom<T, R>(P.g, &sg, &smem)) {   // shared-memory staged tiles
             static bool attr = false;
             const void* k3 = (const void*)hop3_kernel<T, R, E, D>;
             if (!attr) {
@@ -90,7 +91,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
         }
     }
     if constexpr (sizeof(T) == 2 && R == 12) {
-        if (hop_variant() == 5) {   // per-thread shared-memory ring of asynchronous copies
+        if (variant == 5) {   // per-thread shared-memory ring of asynchronous copies
             typedef RingFmt<T, R> RF;
             const void* k5 = (const void*)hop_ring_kernel<T, R, E, D>;
             int per = 0;
@@ -106,7 +107,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
         }
     }
     if constexpr (!std::is_same<T, double>::value) {
-        if (hop_variant() == 2) {   // two sites per thread, packed FP32x2 arithmetic
+        if (variant == 2) {   // two sites per thread, packed FP32x2 arithmetic
             const int n = P.g.Vh / 2;
             const void* k2 = (const void*)hop2_kernel<T, R, E, D>;
             const int nb = (D == RED_NONE) ? stream_blocks(n, block) : reduce_blocks(k2, n, block, nr);
@@ -115,14 +116,14 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
         }
     }
     if constexpr (sizeof(T) == 2) {
-        if (hop_variant() == 6) {   // as 4, with the SU(3) products on FP32x2 column pairs
+        if (variant == 6) {   // as 4, with the SU(3) products on FP32x2 column pairs
             const void* k = (const void*)hop_kernel<T, R, E, D, true, true>;
             const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
             hop_kernel<T, R, E, D, true, true><<<nb * nr, block, 0, s>>>(P);
             return cudaGetLastError();
         }
     }
-    if (hop_variant() == 4) {   // one site per thread, loads one direction ahead
+    if (variant == 4) {   // one site per thread, loads one direction ahead
         const void* k = (const void*)hop_kernel<T, R, E, D, true>;
         const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
         hop_kernel<T, R, E, D, true><<<nb * nr, block, 0, s>>>(P);

@@ -140,6 +140,7 @@ static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, 
                          const uint4* y, double b, const uint4* z, double c, int stage, int guard_kind,
                          cudaStream_t s) {
     HopParams P = hop_params(S, stage, guard_kind);
+    apply_tuning(S.h, WD_FP64, 18, P);
     P.vs = S.vs64;
     P.parity = parity;
     P.links = parity == 0 ? S.le64 : S.lo64;
@@ -167,6 +168,7 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         typedef typename decltype(tag)::type T;
         cudaError_t e;
         HopParams P = hop_params(S, ST_NONE, GUARD_INNER);
+        apply_tuning(h, prec, recon, P);
         P.vs = vs;
         // p := beta (p - omega' v) + r   (gamma of p and v folded in)
         if ((e = Ops<T>::pupdate(n, nr, vs, S.p, S.v, S.r, st, s)) != cudaSuccess) return e;

@@ -53,6 +53,7 @@ def batched(kappa: float, tol: float = 1e-10, stream=None) -> dict:
     res = {}
     d24 = (24, 24, 24, 48)
     lat24 = _lattice(d24, kappa, SMEARED_SEED + 1)
+    lat24.tune("fp16", 12, 12, stream)
     b = torch.stack([synth.to_host_layout(synth.point_source(d24, s, c)) for s in range(4) for c in range(3)]).cuda()
     x = torch.zeros_like(b)
     wd.solve_batch([lat24], [b], [x], tol, "mixed_fp16", stream=stream)        # workspaces and graphs

@@ -28,13 +28,19 @@ SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_pla
 
 # Exported symbols (the declarations of include/wd.h).
 SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_vector_bytes", "wd_pack",
-           "wd_unpack", "wd_apply", "wd_apply_eo_noalloc", "wd_solve_params_default", "wd_solve", "wd_solve_batch",
+           "wd_unpack", "wd_apply", "wd_apply_eo_noalloc", "wd_tune", "wd_solve_params_default", "wd_solve",
+           "wd_solve_batch",
            "wd_precond_set",
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("variant", C.c_int), ("block", C.c_int), ("us", C.c_double), ("default_us", C.c_double),
+                ("candidates", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -75,6 +81,7 @@ def lib():
         L.wd_unpack.argtypes = [vp, i, i, vp, vp, vp]
         L.wd_apply.argtypes = [vp, i, i, i, vp, vp, vp]
         L.wd_apply_eo_noalloc.argtypes = [vp, i, i, vp, vp, vp]
+        L.wd_tune.argtypes = [vp, i, i, i, vp, C.POINTER(TuneResult)]
         L.wd_solve_params_default.argtypes = [i, C.POINTER(SolveParams)]
         L.wd_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
         L.wd_solve_batch.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(vp), d, i,
@@ -174,6 +181,14 @@ class Lattice:
                     "wd_apply")
 
     # --- learned right preconditioner -------------------------------------
+    def tune(self, prec, recon, nrhs=1, stream=None):
+        """wd_tune: pick the fastest hop kernel variant and block size for (prec, recon) on this lattice."""
+        r = TuneResult()
+        self._check(lib().wd_tune(self.h, PREC.get(prec, prec), int(recon), int(nrhs), _stream(stream), C.byref(r)),
+                    "wd_tune")
+        return {"variant": r.variant, "block": r.block, "us": r.us, "default_us": r.default_us,
+                "candidates": r.candidates}
+
     def precond_set(self, w):
         """w: float32 tensor of PRECOND_FLOATS weights (flat layout of wd.h), CPU or CUDA."""
         w = w.to(dtype=__import__("torch").float32).contiguous()

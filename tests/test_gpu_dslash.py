@@ -96,3 +96,26 @@ def test_full_size_sampled_sites(prec, recon):
     assert rel_l2(got[sites], want) <= TOL[prec]
     odd = torch.nonzero(par == 1).reshape(-1)[:1000]
     assert torch.count_nonzero(got[odd]) == 0
+
+
+@pytest.mark.parametrize("prec,recon", [("fp16", 12), ("bf16", 12), ("fp32", 18), ("fp64", 18)])
+def test_tuned_kernels_match_oracle(prec, recon):
+    """wd_tune times every candidate variant and block size and keeps the
+    fastest; every operator then still matches the oracle, and a solve runs
+    on the tuned kernels."""
+    dims = (8, 8, 8, 16)
+    u = synth.gauge_random(dims, 0.5, seed=17)
+    psi = synth.gaussian_source(dims, seed=18)
+    kappa = 0.12
+    lat = lattice(u, kappa, dims)
+    r = lat.tune(prec, recon, nrhs=2)
+    assert r["candidates"] >= 4 and 0 < r["us"] <= r["default_us"]
+    assert r["variant"] in (1, 2, 3, 4, 5, 6) and r["block"] in (64, 128, 256)
+    for op in (wd.WD_OP_HOP_EO, wd.WD_OP_HOP_OE, wd.WD_OP_EO_A, wd.WD_OP_FULL):
+        err = rel_l2(apply_op(lat, prec, recon, op, psi, dims), oracle_op(u, psi, op, kappa))
+        assert err <= TOL[prec], (op, err)
+    if prec == "fp16":
+        b = synth.to_host_layout(psi).cuda()
+        x = torch.zeros_like(b)
+        st = lat.solve(b, x, 1e-10, "mixed_fp16")
+        assert st.status == wd.WD_OK and st.true_residual <= 1e-10
