@@ -182,23 +182,29 @@ int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void* in, void*
 
 /* Result of wd_tune. */
 typedef struct {
-    int variant;          /* hop kernel variant chosen (see wd_tune)                       */
-    int block;            /* threads per block chosen                                      */
-    double us;            /* its average launch time, microseconds                         */
-    double default_us;    /* the default configuration (variant 4, 128 threads)            */
-    int candidates;       /* configurations timed                                          */
+    int variant;          /* plain hop: kernel variant chosen (see wd_tune)                */
+    int block;            /* plain hop: threads per block chosen                           */
+    double us;            /* plain hop: its average launch time, microseconds              */
+    double default_us;    /* plain hop: the default configuration (variant 4, 128 threads) */
+    int candidates;       /* configurations timed per form                                 */
+    int variant_reducing; /* hop with fused epilogue and dot products: variant chosen      */
+    int block_reducing;   /* ... threads per block chosen                                  */
+    double us_reducing;   /* ... its average launch time, microseconds                     */
 } wd_tune_result;
 
 /* Autotune the hopping kernel H_eo (Eq. 1) of storage precision `prec` with
- * link format `recon` for batches of `nrhs` right-hand sides on this lattice:
- * times every candidate kernel variant and block size on scratch vectors
- * (2 warm-up and 8 timed launches each, CUDA events on `stream`) and keeps the
- * fastest for every later wd_apply / wd_solve / wd_solve_batch of the handle
- * in that (prec, recon); captured solver graphs are rebuilt. Candidates:
- * variant 4 (one site per thread, loads one direction ahead; 64, 128, 256
- * threads), 1 (no look-ahead), 2 (two sites per thread, FP32x2; not FP64),
+ * link format `recon` for batches of `nrhs` right-hand sides on this lattice,
+ * separately for its two forms in the solvers (the plain hop, and the hop with
+ * fused epilogue and dot products that ends each even-odd operator): times
+ * every candidate kernel variant and block size on scratch vectors (2 warm-up
+ * and 8 timed launches each, CUDA events on `stream`) and keeps the fastest
+ * for every later wd_apply / wd_solve / wd_solve_batch of the handle in that
+ * (prec, recon); captured solver graphs are rebuilt. Candidates:
+ * variant 4 (one site per thread, loads one direction ahead; 64 and 128
+ * threads, and 256 except for FP16), 1 (no look-ahead), 2 (two sites per
+ * thread, FP32x2; not FP64),
  * and for 16-bit storage 3 (tiles staged in shared memory), 6 (FP32x2 column
- * pairs; 128, 256 threads) and, with 12-real links, 5 (per-thread cp.async
+ * pairs; 64, 128 threads, and 256 for BF16) and, with 12-real links, 5 (per-thread cp.async
  * ring). Not a feature of the paper. Synchronizes `stream`; allocates two
  * scratch vectors of nrhs parity vectors. `out` may be NULL. */
 int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream, wd_tune_result* out);

@@ -9,8 +9,16 @@
 
 namespace wd {
 
-static int g_hop_block = 128;
-int hop_block() { return g_hop_block; }
+static int g_hop_block = 0;
+// Default threads per block of the hop kernels: environment WD_HOP_BLOCK (64 or 128), else 128.
+int hop_block() {
+    if (g_hop_block == 0) {
+        const char* e = std::getenv("WD_HOP_BLOCK");
+        const int b = e ? std::atoi(e) : 0;
+        g_hop_block = (b == 64 || b == 128) ? b : 128;
+    }
+    return g_hop_block;
+}
 void set_hop_block(int b) { g_hop_block = b; }
 
 int hop_variant() {

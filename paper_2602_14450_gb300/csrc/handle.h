@@ -56,8 +56,9 @@ struct wd_handle {
     bool have_precond = false;         // weights of the learned preconditioner loaded
     long long adam_t = 0;              // Adam steps taken on those weights
 
-    int tune_variant[4][2] = {};       // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1]; 0 = default
-    int tune_block[4][2] = {};
+    // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1][without / with fused reduction]; 0 = default
+    int tune_variant[4][2][2] = {};
+    int tune_block[4][2][2] = {};
 };
 
 namespace wd {
@@ -73,8 +74,10 @@ size_t vec_bytes(const wd_handle* h, int prec);
 RedCtx red_ctx(wd_handle* h, int stage);
 // Hop kernel configuration chosen by wd_tune for (prec, recon), if any.
 inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) {
-    P.variant = h->tune_variant[prec][recon == 12 ? 0 : 1];
-    P.block = h->tune_block[prec][recon == 12 ? 0 : 1];
+    for (int f = 0; f < 2; ++f) {
+        P.variant[f] = h->tune_variant[prec][recon == 12 ? 0 : 1][f];
+        P.block[f] = h->tune_block[prec][recon == 12 ? 0 : 1][f];
+    }
 }
 
 }  // namespace wd

@@ -31,8 +31,9 @@ struct HopParams {
     const SolverState* guard;  // per-rhs state consulted by the guard
     int guard_kind;            // GuardKind
     int* err;                  // set to 1 by a kernel whose bounded wait gave up (may be null)
-    int variant;               // kernel variant (hop_variant() numbering); 0 = the process default
-    int block;                 // threads per block; 0 = the process default
+    int variant[2];            // kernel variant (hop_variant() numbering) without / with a fused
+                               // reduction; 0 = the process default
+    int block[2];              // threads per block, likewise; 0 = the process default
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.
@@ -72,7 +73,8 @@ template <typename T> struct Ops {
 cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* out, cudaStream_t s);
 
 // Block size of every vector kernel; the hop kernels take theirs from
-// hop_block() (default 128).
+// HopParams::block (set by wd_tune) or else hop_block() (environment
+// WD_HOP_BLOCK = 64 or 128, default 128).
 constexpr int VEC_BLOCK = 256;
 int hop_block();
 void set_hop_block(int b);

@@ -66,8 +66,9 @@ bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
 
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
-    const int block = P.block > 0 ? P.block : hop_block();
-    const int variant = P.variant > 0 ? P.variant : hop_variant();
+    constexpr int form = D == RED_NONE ? 0 : 1;
+    const int block = P.block[form] > 0 ? P.block[form] : hop_block();
+    const int variant = P.variant[form] > 0 ? P.variant[form] : hop_variant();
     const int nr = P.nrhs;
     if constexpr (sizeof(T) == 2) {
         StageGeom sg;

@@ -1,5 +1,7 @@
 // wd_tune: per-handle choice of the hopping-kernel variant and block size by
-// timing every candidate on this lattice (CUDA events on the caller's stream).
+// timing every candidate on this lattice (CUDA events on the caller's stream),
+// separately for the plain hop and for the hop with fused epilogue and dot
+// products that ends every even-odd operator of the inner solve.
 #include <vector>
 
 #include "handle.h"
@@ -13,12 +15,14 @@ struct Cand {
 };
 
 std::vector<Cand> candidates(int prec, int recon) {
-    std::vector<Cand> c = {{4, 128}, {4, 64}, {4, 256}, {1, 128}};
+    std::vector<Cand> c = {{4, 128}, {4, 64}, {1, 128}};
+    if (prec != WD_FP16) c.push_back({4, 256});   // the plain FP16 look-ahead kernel takes at most 128 threads
     if (prec != WD_FP64) c.push_back({2, 128});
     if (prec == WD_FP16 || prec == WD_BF16) {
         c.push_back({3, 128});
         c.push_back({6, 128});
-        c.push_back({6, 256});
+        c.push_back({6, 64});
+        if (prec == WD_BF16) c.push_back({6, 256});
         if (recon == 12) c.push_back({5, 128});
     }
     return c;
@@ -33,13 +37,16 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
     const uint4 *le, *lo;
     int rc = ensure_links(h, prec, recon, &le, &lo);
     if (rc != WD_OK) return rc;
+    if ((rc = ensure_solver_state(h, nrhs)) != WD_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vb = vec_bytes(h, prec) * (size_t)nrhs;
     uint4* in = (uint4*)workspace(h, "tune.in", vb);
+    uint4* y = (uint4*)workspace(h, "tune.y", vb);
     uint4* outv = (uint4*)workspace(h, "tune.out", vb);
-    if (!in || !outv) return fail(h, WD_ERR_CUDA, "out of device memory");
+    if (!in || !y || !outv) return fail(h, WD_ERR_CUDA, "out of device memory");
     // a byte pattern of ordinary finite values in every storage format (0x3C3C = 1.06 in FP16)
     WD_CUDA(h, cudaMemsetAsync(in, 0x3C, vb, s));
+    WD_CUDA(h, cudaMemsetAsync(y, 0x3C, vb, s));
     HopParams P{};
     P.g = h->g;
     P.nrhs = nrhs;
@@ -48,52 +55,63 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
     P.links = le;
     P.in = in;
     P.out = outv;
+    P.y = y;
     P.a = 1.0;
+    P.b = 1.0;
     P.guard_kind = GUARD_NONE;
+    P.rc = red_ctx(h, ST_NONE);   // the last block of a reduction finds no scalar stage to run
     cudaEvent_t e0, e1;
     WD_CUDA(h, cudaEventCreate(&e0));
     WD_CUDA(h, cudaEventCreate(&e1));
     const std::vector<Cand> cands = candidates(prec, recon);
-    Cand best = cands[0];
-    float best_ms = 1e30f, default_ms = 0.f;
+    Cand best[2] = {cands[0], cands[0]};
+    float best_ms[2] = {1e30f, 1e30f}, default_ms = 0.f;
     cudaError_t err = cudaSuccess;
-    for (const Cand& c : cands) {
-        P.variant = c.variant;
-        P.block = c.block;
-        auto launch = [&]() {
-            return by_prec(prec, [&](auto tag) {
-                typedef typename decltype(tag)::type T;
-                return Ops<T>::hop(recon, EPI_H, RED_NONE, P, s);
-            });
-        };
-        for (int i = 0; i < 2 && err == cudaSuccess; ++i) err = launch();
-        if (err == cudaSuccess) err = cudaEventRecord(e0, s);
-        for (int i = 0; i < 8 && err == cudaSuccess; ++i) err = launch();
-        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err != cudaSuccess) break;
-        ms /= 8.f;
-        if (c.variant == 4 && c.block == 128) default_ms = ms;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
+    for (int form = 0; form < 2 && err == cudaSuccess; ++form) {
+        for (const Cand& c : cands) {
+            P.variant[form] = c.variant;
+            P.block[form] = c.block;
+            auto launch = [&]() {
+                return by_prec(prec, [&](auto tag) {
+                    typedef typename decltype(tag)::type T;
+                    return form == 0 ? Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)
+                                     : Ops<T>::hop(recon, EPI_Y, RED_TS, P, s);
+                });
+            };
+            for (int i = 0; i < 2 && err == cudaSuccess; ++i) err = launch();
+            if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+            for (int i = 0; i < 8 && err == cudaSuccess; ++i) err = launch();
+            if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            ms /= 8.f;
+            if (form == 0 && c.variant == 4 && c.block == 128) default_ms = ms;
+            if (ms < best_ms[form]) {
+                best_ms[form] = ms;
+                best[form] = c;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(h, err, "wd_tune: timing a candidate");
     const int ri = recon == 12 ? 0 : 1;
-    h->tune_variant[prec][ri] = best.variant;
-    h->tune_block[prec][ri] = best.block;
+    for (int form = 0; form < 2; ++form) {
+        h->tune_variant[prec][ri][form] = best[form].variant;
+        h->tune_block[prec][ri][form] = best[form].block;
+    }
     h->gen += 1;   // captured solver graphs hold the old kernels
     if (out) {
-        out->variant = best.variant;
-        out->block = best.block;
-        out->us = 1e3 * best_ms;
+        out->variant = best[0].variant;
+        out->block = best[0].block;
+        out->us = 1e3 * best_ms[0];
         out->default_us = 1e3 * default_ms;
         out->candidates = (int)cands.size();
+        out->variant_reducing = best[1].variant;
+        out->block_reducing = best[1].block;
+        out->us_reducing = 1e3 * best_ms[1];
     }
     return WD_OK;
 }

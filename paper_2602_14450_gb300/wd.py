@@ -40,7 +40,8 @@ PRECOND_FLOATS = 6912
 
 class TuneResult(C.Structure):
     _fields_ = [("variant", C.c_int), ("block", C.c_int), ("us", C.c_double), ("default_us", C.c_double),
-                ("candidates", C.c_int)]
+                ("candidates", C.c_int), ("variant_reducing", C.c_int), ("block_reducing", C.c_int),
+                ("us_reducing", C.c_double)]
 
 
 class SolveParams(C.Structure):
@@ -187,7 +188,8 @@ class Lattice:
         self._check(lib().wd_tune(self.h, PREC.get(prec, prec), int(recon), int(nrhs), _stream(stream), C.byref(r)),
                     "wd_tune")
         return {"variant": r.variant, "block": r.block, "us": r.us, "default_us": r.default_us,
-                "candidates": r.candidates}
+                "candidates": r.candidates, "variant_reducing": r.variant_reducing,
+                "block_reducing": r.block_reducing, "us_reducing": r.us_reducing}
 
     def precond_set(self, w):
         """w: float32 tensor of PRECOND_FLOATS weights (flat layout of wd.h), CPU or CUDA."""
