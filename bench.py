@@ -26,7 +26,7 @@ if ROOT not in sys.path:
 # DRAM bytes (read + write) of one launch of the FP16 12-real hop at 32^3 x 64,
 # from the ncu capture summarised in profiles/hop_fp16_12_32x32x32x64.md; set
 # to None whenever that kernel changes until it is captured again.
-HOP_FP16_12_TRAFFIC = None
+HOP_FP16_12_TRAFFIC = 269_941_248
 
 METRIC = "time to ‖r‖/‖b‖≤1e-10 at 32^3×64, FP16-mixed vs FP64; Dslash GB/s vs HBM peak"
 TOL = 1e-10
