@@ -208,3 +208,4 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
            "fp64": run("fp64")}
     lat.close()
     return out
+
