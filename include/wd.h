@@ -111,6 +111,16 @@ typedef struct wd_solve_params {
     int recon;            /* link format of the inner operator: 12 or 18                     */
     int ftz;              /* flush subnormal low-precision values to zero on store           */
     int iters_per_sync;   /* inner iterations captured per CUDA-graph launch                 */
+    double* history;      /* optional host array of history_cap entries of 4 doubles, filled
+                             for a solve of one system with one right-hand side (wd_solve)
+                             with the convergence history:
+                             {kind, matvecs, residual, nonzeros}; kind 1 = a refinement trip
+                             (residual = |b^ - A x| / |eta| in FP64 at its start, nonzeros =
+                             nonzero reals of its low-precision input), kind 0 = an inner
+                             BiCGStab iteration (residual = its |r| / gamma' mapped to the
+                             outer scale, (|r| / gamma') |r_outer| / (s^ |eta|)); matvecs =
+                             low-precision matvecs so far. NULL = none                       */
+    int history_cap;      /* entries `history` holds                                         */
 } wd_solve_params;
 
 /* Counters of one solve. */
@@ -125,6 +135,7 @@ typedef struct wd_solve_stats {
     double elapsed_ms;         /* device time of the whole solve (CUDA events)           */
     long long first_inner_nonzeros; /* nonzero reals of the first low-precision input    */
     long long kernel_launches; /* device kernels this call launched (graph nodes included) */
+    int history_len;           /* entries written to params->history                     */
 } wd_solve_stats;
 
 /* Create a lattice handle. dims: 4 even extents >= 2, Lx*Ly*Lz*Lt/2 < 2^31.

@@ -283,6 +283,8 @@ struct SolverState {
     int iter, matvecs, first, done, status;
     int skip;                       // right-hand side finished: every kernel leaves it alone
     int ftz;                        // flush subnormal values of every low-precision store
+    double* hist;                   // optional device log: (matvecs, |r|/gamma') per inner iteration
+    int hist_cap;                   // iterations the log holds
     // refinement (outer) scalars
     double rnorm;                   // |b^ - A x| of the FP64 outer residual
     double shat;                    // |single(y~)|
@@ -353,6 +355,10 @@ __device__ inline void end_iteration(SolverState* st, double gamma, double rn2, 
     st->matvecs += 2;
     st->first = 0;
     st->res = sqrt(rn2) / st->gamma_p;
+    if (st->hist && st->iter <= st->hist_cap) {
+        st->hist[2 * (st->iter - 1)] = (double)st->matvecs;
+        st->hist[2 * (st->iter - 1) + 1] = st->res;
+    }
     if (!(isfinite(st->res) && finite2(st->cP) && finite2(st->cV) && isfinite(st->gamma_p))) {
         stop(st, S_NONFINITE);
         return;

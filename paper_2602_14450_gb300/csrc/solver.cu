@@ -360,6 +360,29 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
 
     std::vector<int> status(total_rhs, WD_OK);
     int trips = 0;
+
+    // convergence history (one system with one right-hand side): device log of
+    // the inner iterations of a trip, copied out and mapped after each trip
+    const bool hist_on = prm.history && prm.history_cap > 0 && sys.size() == 1 && sys[0].nrhs == 1;
+    const int hist_iters = prm.max_inner / 2 + 2;
+    double* dhist = nullptr;
+    if (hist_on) {
+        dhist = (double*)workspace(h0, "hist", sizeof(double) * 2 * hist_iters);
+        if (!dhist) return fail(h0, WD_ERR_CUDA, "out of device memory (history)");
+    }
+    std::vector<double> hbuf;
+    int hlen = 0;
+    long long hcum = 0;                 // low-precision matvecs so far
+    double trip_res = 0.0, trip_rn = 0.0;
+    auto hist_put = [&](double kind, double mv, double res, double nz) {
+        if (hlen >= prm.history_cap) return;
+        double* e = prm.history + 4 * (size_t)hlen++;
+        e[0] = kind;
+        e[1] = mv;
+        e[2] = res;
+        e[3] = nz;
+    };
+
     for (;;) {
         // decide, per right-hand side, whether to continue (outer stopping rule)
         bool any = false;
@@ -382,6 +405,11 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                 }
                 S.active[r] = act;
                 q.skip = act ? 0 : 1;
+                if (hist_on) {
+                    trip_rn = rn;
+                    trip_res = en > 0 ? rn / en : 0.0;
+                    if (!act) hist_put(1.0, (double)hcum, trip_res, 0.0);   // the final residual
+                }
                 if (act) {
                     any = true;
                     q.s = prm.s;
@@ -393,6 +421,8 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                     q.rescale_x = prm.rescale_x;
                     q.scale_pass = scale_pass ? 1 : 0;
                     q.ftz = prm.ftz ? 1 : 0;
+                    q.hist = hist_on ? dhist : nullptr;
+                    q.hist_cap = hist_on ? hist_iters : 0;
                     q.max_matvecs = prm.max_inner;
                     // FP64 BiCGStab: one inner solve to the outer tolerance; mixed: eps of Table 2
                     q.eps = cfg.fp64_inner ? std::max(0.5 * tol * en / rn, 1e-15) : prm.inner_eps;
@@ -452,6 +482,17 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                 out[k].outer_matvecs += 1;
                 if (out[k].outer_iterations == 1) out[k].first_inner_nonzeros = q.nonzeros;
                 if (q.status == S_NONFINITE) status[k] = WD_ERR_NONFINITE;
+                if (hist_on) {
+                    hist_put(1.0, (double)hcum, trip_res, (double)q.nonzeros);
+                    const int ni = q.iter < hist_iters ? q.iter : hist_iters;
+                    hbuf.resize(2 * (size_t)(ni > 0 ? ni : 1));
+                    if (ni > 0)
+                        WD_CUDA(S.h, cudaMemcpy(hbuf.data(), dhist, sizeof(double) * 2 * ni, cudaMemcpyDeviceToHost));
+                    const double en = S.eta_norm[r];
+                    const double map = (q.shat > 0 && en > 0) ? trip_rn / (q.shat * en) : 0.0;
+                    for (int i = 0; i < ni; ++i) hist_put(0.0, (double)hcum + hbuf[2 * i], hbuf[2 * i + 1] * map, 0.0);
+                    hcum += q.matvecs;
+                }
             }
         }
     }
@@ -496,6 +537,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             wd_solve_stats& o = out[k];
             o.elapsed_ms = ms;
             o.kernel_launches = nk;
+            o.history_len = hist_on ? hlen : 0;
             o.true_residual = en > 0 ? std::sqrt(S.h->hst[r].acc) / en : 0.0;
             if (o.outer_iterations == 0) o.first_inner_nonzeros = -1;
             int st = status[k];

@@ -48,14 +48,16 @@ class SolveParams(C.Structure):
     _fields_ = [("s", C.c_double), ("sigma", C.c_double), ("sigma_lambda", C.c_double),
                 ("inner_eps", C.c_double), ("omega0", C.c_double), ("recalc_gamma", C.c_int),
                 ("rescale_x", C.c_int), ("use_shat", C.c_int), ("x_is_guess", C.c_int), ("max_outer", C.c_int),
-                ("max_inner", C.c_int), ("recon", C.c_int), ("ftz", C.c_int), ("iters_per_sync", C.c_int)]
+                ("max_inner", C.c_int), ("recon", C.c_int), ("ftz", C.c_int), ("iters_per_sync", C.c_int),
+                ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iterations", C.c_int), ("inner_iterations", C.c_int),
                 ("inner_matvecs", C.c_int), ("outer_matvecs", C.c_int), ("true_residual", C.c_double),
                 ("outer_residual", C.c_double), ("elapsed_ms", C.c_double),
-                ("first_inner_nonzeros", C.c_longlong), ("kernel_launches", C.c_longlong)]
+                ("first_inner_nonzeros", C.c_longlong), ("kernel_launches", C.c_longlong),
+                ("history_len", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -234,6 +236,21 @@ class Lattice:
         if check:
             self._check(rc, "wd_solve")
         return st
+
+
+def solve_with_history(lat, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, cap=100000):
+    """wd_solve with the convergence history: returns (stats, rows) with rows a list of
+    (kind, matvecs, residual, nonzeros); kind 1 = refinement trip, 0 = inner iteration."""
+    sc = SCHEME.get(scheme, scheme)
+    prm = params if params is not None else default_params(sc)
+    buf = (C.c_double * (4 * cap))()
+    prm.history = C.cast(buf, C.POINTER(C.c_double))
+    prm.history_cap = cap
+    st = lat.solve(b, x, tol, scheme, prm, stream, check=False)
+    rows = [tuple(buf[4 * i: 4 * i + 4]) for i in range(st.history_len)]
+    prm.history = None
+    prm.history_cap = 0
+    return st, rows
 
 
 def solve_batch(lattices, bs, xs, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):

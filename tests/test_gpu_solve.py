@@ -229,3 +229,29 @@ def test_full_size_solution_sampled_residual():
         xs = from_lex(x, wl.dims)
         r = eta_s - (xs.reshape(-1, 4, 3)[sites] - wl.kappa * W.hop_at_sites(u, xs, sites, BC))
         assert S.norm(r) / S.norm(eta_s) <= 3 * TOL, scheme
+
+
+def test_convergence_history(cfg0):
+    """The solve's history (Figs. 4-6 style): one entry per refinement trip and
+    per inner iteration, matvecs increasing, the final entry equal to the
+    reported outer residual, and each trip's last inner residual, mapped to the
+    outer scale, within a small factor of the next trip's FP64 residual."""
+    dims, u, eta, kappa, ref = cfg0
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    x = torch.zeros_like(b)
+    st, rows = wd.solve_with_history(lat, b, x, TOL, "mixed_fp16")
+    assert st.status == wd.WD_OK and st.history_len == len(rows)
+    trips = [r for r in rows if r[0] == 1.0]
+    inner = [r for r in rows if r[0] == 0.0]
+    assert len(trips) == st.outer_iterations + 1 and len(inner) == st.inner_iterations
+    mv = [r[1] for r in rows]
+    assert all(a <= b2 for a, b2 in zip(mv, mv[1:])) and mv[-1] == st.inner_matvecs
+    assert abs(trips[-1][2] - st.outer_residual) <= 1e-12 * max(1.0, st.outer_residual)
+    assert trips[0][3] == st.first_inner_nonzeros
+    # last inner estimate of each trip against the FP64 residual that starts the next one
+    idx = [i for i, r in enumerate(rows) if r[0] == 1.0]
+    for i0, i1 in zip(idx, idx[1:]):
+        if i1 - 1 > i0:
+            est, nxt = rows[i1 - 1][2], rows[i1][2]
+            assert nxt / 10 <= est <= nxt * 10, (est, nxt)
