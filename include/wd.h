@@ -156,6 +156,29 @@ int wd_set_gauge(wd_handle* h, const double* U, int where);
  * gauge field (FP64). 12-real formats are refused when either exceeds 1e-6. */
 int wd_gauge_unitarity(wd_handle* h, double* max_unitarity_dev, double* max_det_dev);
 
+/* Add the clover (Sheikholeslami-Wohlert) term to the matrix of the handle:
+ * D_sw = C - kappa H with the site-local 12 x 12 Hermitian blocks
+ *   C(x) = 1 - c_sw kappa sum_{mu<nu} sigma_mu_nu (x) Fh_mu_nu(x),
+ * sigma_mu_nu = (i/2) [gamma_mu, gamma_nu] (the gamma matrices of this
+ * header), Fh_mu_nu = traceless part of (Q_mu_nu - Q_mu_nu^+) / (8 i) and
+ * Q_mu_nu(x) the four plaquettes of the mu-nu plane with a corner at x, each
+ * traversed mu-then-nu; the links are periodic. The paper uses the plain
+ * Wilson matrix and names the clover matrix as the next one to study
+ * (Sec. 6); its even-odd system (Eqs. 4-5) takes the blocks as D_ee, D_oo:
+ *   A = 1 - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe,
+ *   b^ = C_ee^-1 (eta_e + kappa H_eo C_oo^-1 eta_o),
+ *   xi_o = C_oo^-1 (eta_o + kappa H_oe xi_e).
+ * Afterwards wd_apply (WD_OP_EO_A, WD_OP_FULL) and the solvers use D_sw (the
+ * hopping operators WD_OP_HOP_* are unchanged); the refinement stops when
+ * |b^ - A xi_e| <= tol |eta| / (1 + 12 |c_sw| kappa), which bounds the full
+ * residual |eta - D_sw xi| = |C_ee (b^ - A xi_e)| by tol |eta|. C and C^-1
+ * are computed in FP64 on the device (Gauss-Jordan per site) and converted
+ * to other precisions on first use; wd_set_gauge rebuilds them. c_sw = 0
+ * removes the term. Not available with WD_MIXED_FP16_LEARNED. Requires
+ * wd_set_gauge first (WD_ERR_NO_GAUGE); WD_ERR_INVALID_ARG for a non-finite
+ * c_sw or a singular block. */
+int wd_set_clover(wd_handle* h, double csw);
+
 /* Bytes of one packed parity vector in precision `prec` (24 * V/2 reals). */
 size_t wd_vector_bytes(const wd_handle* h, int prec);
 

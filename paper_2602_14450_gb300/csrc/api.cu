@@ -287,6 +287,7 @@ int wd_set_gauge(wd_handle* h, const double* U, int where) {
     std::memcpy(&h->unit_dev, &host[0], sizeof(double));
     std::memcpy(&h->det_dev, &host[1], sizeof(double));
     h->have_gauge = true;
+    if (h->have_clover) return clover_build(h);   // the clover blocks follow the links
     return WD_OK;
 }
 
@@ -347,7 +348,15 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     P.guard_kind = GUARD_NONE;
     apply_tuning(h, prec, recon, P);
     const double k = h->kappa;
-    auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y) {
+    const uint4 *ci_e = nullptr, *ci_o = nullptr, *cf_e = nullptr, *cf_o = nullptr;
+    if (h->have_clover && (op == WD_OP_EO_A || op == WD_OP_FULL)) {
+        if ((rc = ensure_clover(h, prec, op == WD_OP_EO_A ? 0 : 1, op == WD_OP_EO_A ? &ci_e : &cf_e,
+                                op == WD_OP_EO_A ? &ci_o : &cf_o)) != WD_OK)
+            return rc;
+    }
+    auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y,
+                   const uint4* mat = nullptr) {
+        P.mat = mat;
         P.parity = parity;
         P.links = parity == 0 ? le : lo;
         P.in = (const uint4*)src;
@@ -366,18 +375,31 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     switch (op) {
     case WD_OP_HOP_EO: e = hop(0, in, out, EPI_H, 1.0, 0.0, nullptr); break;
     case WD_OP_HOP_OE: e = hop(1, in, out, EPI_H, 1.0, 0.0, nullptr); break;
-    case WD_OP_EO_A: {
+    case WD_OP_EO_A: {   // with clover: in - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe in (Eq. 4)
         void* tmp = workspace(h, "apply.tmp." + std::to_string(prec), half);
         if (!tmp) return fail(h, WD_ERR_CUDA, "out of device memory");
-        e = hop(1, in, tmp, EPI_H, 1.0, 0.0, nullptr);
-        if (e == cudaSuccess) e = hop(0, tmp, out, EPI_Y, -k * k, 1.0, in);
+        e = hop(1, in, tmp, EPI_H, 1.0, 0.0, nullptr, ci_o);
+        if (e == cudaSuccess) e = hop(0, tmp, out, EPI_Y, -k * k, 1.0, in, ci_e);
         break;
     }
-    case WD_OP_FULL: {
+    case WD_OP_FULL: {   // with clover: C in - kappa H in on both parities
         const char* ie = (const char*)in;
         char* oe = (char*)out;
-        e = hop(0, ie + half, oe, EPI_Y, -k, 1.0, ie);
-        if (e == cudaSuccess) e = hop(1, ie, oe + half, EPI_Y, -k, 1.0, ie + half);
+        const void* ye = ie;
+        const void* yo = ie + half;
+        if (cf_e) {   // out = C in first, then the hop adds to it in place
+            e = by_prec(prec, [&](auto tag) {
+                typedef typename decltype(tag)::type T;
+                cudaError_t r2 = Ops<T>::apply_mat(h->g.Vh, 1, 0, cf_e, (const uint4*)ie, (uint4*)oe, s);
+                if (r2 == cudaSuccess)
+                    r2 = Ops<T>::apply_mat(h->g.Vh, 1, 0, cf_o, (const uint4*)(ie + half), (uint4*)(oe + half), s);
+                return r2;
+            });
+            ye = oe;
+            yo = oe + half;
+        }
+        if (e == cudaSuccess) e = hop(0, ie + half, oe, EPI_Y, -k, 1.0, ye);
+        if (e == cudaSuccess) e = hop(1, ie, oe + half, EPI_Y, -k, 1.0, yo);
         break;
     }
     }

@@ -247,6 +247,43 @@ __global__ void __launch_bounds__(256) k_rescale_in(int n, int nrhs, long long v
     grid_reduce<2>(v, rc, sl);
 }
 
+// out = M in site by site (M: 12 x 12 complex blocks of one parity, shared by all right-hand sides)
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_mat(int n, int nrhs, long long vs, const uint4* mat, const uint4* in,
+                                                   uint4* out) {
+    typedef typename Unit<T>::C C;
+    const Slice sl = slice_of(nrhs);
+    in += sl.rhs * vs;
+    out += sl.rhs * vs;
+    RHS_LOOP(h, n) {
+        C v[24], o[24];
+        load_spinor<T>(in, n, h, v);
+        mat_mul<T>(mat, n, h, v, o);
+        store_spinor<T>(out, n, h, o);
+    }
+}
+
+// Blocks of storage T from FP64 blocks: 288 reals per site, element e of site h
+// in unit e / N of the block array (units n apart), as for spinors.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mat_from64(int n, const uint4* src, uint4* dst) {
+    typedef typename Unit<T>::C C;
+    constexpr int N = Unit<T>::N;
+    GRID_STRIDE(h, n) {
+#pragma unroll 1
+        for (int u = 0; u < 288 / N; ++u) {
+            C v[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int e = u * N + i;
+                const uint4 w = src[(size_t)(e / 2) * n + h];
+                v[i] = (C)Unit<double>::get(w, e % 2);
+            }
+            dst[(size_t)u * n + h] = Unit<T>::put(v);
+        }
+    }
+}
+
 // x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 2 correction; Alg. 1: s^ -> s)
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(int n, int nrhs, long long vs, long long vs64, uint4* x64,

@@ -152,6 +152,33 @@ __device__ __forceinline__ void store_spinor(uint4* v, int stride, int h, typena
     }
 }
 
+// out = M v for the site-local 12 x 12 complex matrix M of site h (row-major,
+// spin-colour index 3 s + a, the layout of the clover blocks): row i is the
+// 24 reals of units i * SU .. i * SU + SU - 1 (SU = units of a spinor).
+template <typename T>
+__device__ __forceinline__ void mat_mul(const uint4* __restrict__ mat, int stride, int h,
+                                        const typename Unit<T>::C (&v)[24], typename Unit<T>::C (&out)[24]) {
+    typedef typename Unit<T>::C C;
+    constexpr int SU = 24 / Unit<T>::N;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        C row[24];
+        load_spinor<T>(mat + (size_t)i * SU * stride, stride, h, row);
+        C re = row[0] * v[0], im = row[0] * v[1];
+        re = fma(-row[1], v[1], re);
+        im = fma(row[1], v[0], im);
+#pragma unroll
+        for (int j = 1; j < 12; ++j) {
+            re = fma(row[2 * j], v[2 * j], re);
+            re = fma(-row[2 * j + 1], v[2 * j + 1], re);
+            im = fma(row[2 * j], v[2 * j + 1], im);
+            im = fma(row[2 * j + 1], v[2 * j], im);
+        }
+        out[2 * i] = re;
+        out[2 * i + 1] = im;
+    }
+}
+
 // --------------------------------------------------------------- geometry ---
 
 // Division of a non-negative int below 2^31 by a fixed divisor d in

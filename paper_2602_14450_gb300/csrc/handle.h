@@ -1,6 +1,7 @@
 // Internal state behind the opaque wd_handle of the C ABI.
 #pragma once
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
@@ -56,6 +57,10 @@ struct wd_handle {
     bool have_precond = false;         // weights of the learned preconditioner loaded
     long long adam_t = 0;              // Adam steps taken on those weights
 
+    double csw = 0.0;                  // clover coefficient of wd_set_clover (0: plain Wilson)
+    bool have_clover = false;
+    uint4* clov[2][4][2] = {};         // clover blocks [C^-1, C][prec][parity], built on first use
+
     // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1][without / with fused reduction]; 0 = default
     int tune_variant[4][2][2] = {};
     int tune_block[4][2][2] = {};
@@ -72,6 +77,12 @@ int ensure_solver_state(wd_handle* h, int nrhs);
 int ensure_links(wd_handle* h, int prec, int recon, const uint4** even, const uint4** odd);
 size_t vec_bytes(const wd_handle* h, int prec);
 RedCtx red_ctx(wd_handle* h, int stage);
+// Clover blocks (clover.cu): rebuild from the gauge field; fetch kind 0 (C^-1)
+// or 1 (C) in a precision (null pointers without a clover term).
+int clover_build(wd_handle* h);
+int ensure_clover(wd_handle* h, int prec, int kind, const uint4** even, const uint4** odd);
+// 1 + 12 |c_sw| kappa bounds the norm of every clover block C.
+inline double clover_bound(const wd_handle* h) { return h->have_clover ? 1.0 + 12.0 * std::fabs(h->csw) * h->kappa : 1.0; }
 // Hop kernel configuration chosen by wd_tune for (prec, recon), if any.
 inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) {
     for (int f = 0; f < 2; ++f) {

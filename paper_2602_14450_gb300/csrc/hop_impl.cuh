@@ -211,7 +211,7 @@ __device__ __forceinline__ void link_mul(const uint4 (&u)[LinkFmt<T, R>::GROUP_U
 
 // Epilogue of one output site: out = a * acc + b * y + c * z, rounded to
 // storage and written, and this thread's share of the fused dot products.
-template <typename T, int EPI, int RED>
+template <typename T, int EPI, int RED, bool MAT = false>
 __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, const uint4* vy, const uint4* vz,
                                              const uint4* vrs, int h, typename Unit<T>::C (&acc)[24],
                                              typename Unit<T>::C (&part)[RedSums<RED>::N], bool ftz) {
@@ -219,6 +219,12 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, co
     constexpr int NS = RedSums<RED>::N;
     const int Vh = P.g.Vh;
     const C ca = (C)P.a, cb = (C)P.b, cc = (C)P.c;
+    if constexpr (MAT) {   // the site-local block (clover, Eqs. 4-5) applied to the hop
+        C t[24];
+        mat_mul<T>(P.mat, Vh, h, acc, t);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = t[i];
+    }
     C o[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) o[i] = (EPI == EPI_H && P.a == 1.0) ? acc[i] : ca * acc[i];
@@ -327,14 +333,14 @@ __device__ __forceinline__ void link_mul_pair(const uint4 (&u)[LinkFmt<T, R>::GR
 // reduction fit 72 registers (7 blocks of 128 threads per SM; measured 3%
 // faster, while BF16 there is 6% slower), the other 16-bit kernels keep 80
 // (3 blocks of 256); FP32 128 and FP64 255 registers.
-template <typename T, int RED, bool PF> struct HopBounds {
-    static constexpr bool LEAN = std::is_same<T, __half>::value && PF && RED == RED_NONE;
+template <typename T, int RED, bool PF, bool MAT = false> struct HopBounds {
+    static constexpr bool LEAN = std::is_same<T, __half>::value && PF && RED == RED_NONE && !MAT;
     static constexpr int THREADS = LEAN ? 128 : 256;
     static constexpr int MIN_BLOCKS = LEAN ? 7 : sizeof(T) == 2 ? (PF ? 3 : 2) : sizeof(T) == 4 ? 2 : 1;
 };
 
-template <typename T, int R, int EPI, int RED, bool PF, bool PAIR = false>
-__global__ void __launch_bounds__(HopBounds<T, RED, PF>::THREADS, HopBounds<T, RED, PF>::MIN_BLOCKS)
+template <typename T, int R, int EPI, int RED, bool PF, bool PAIR = false, bool MAT = false>
+__global__ void __launch_bounds__(HopBounds<T, RED, PF, MAT>::THREADS, HopBounds<T, RED, PF, MAT>::MIN_BLOCKS)
     hop_kernel(const HopParams P) {
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(HopBounds<T, RED, PF>::THREADS, HopBounds<T, R
             }
         }
 
-        hop_epilogue<T, EPI, RED>(P, vout, vy, vz, vrs, h, acc, part, ftz);
+        hop_epilogue<T, EPI, RED, MAT>(P, vout, vy, vz, vrs, h, acc, part, ftz);
     }
 
     if constexpr (RED != RED_NONE) {

@@ -66,6 +66,13 @@ bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
 
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
+    if (P.mat) {   // with a site-local block (clover): the one-site-per-thread look-ahead kernel
+        const int blk = 128;
+        const void* km = (const void*)hop_kernel<T, R, E, D, true, false, true>;
+        const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);
+        hop_kernel<T, R, E, D, true, false, true><<<nb * P.nrhs, blk, 0, s>>>(P);
+        return cudaGetLastError();
+    }
     constexpr int form = D == RED_NONE ? 0 : 1;
     const int block = P.block[form] > 0 ? P.block[form] : hop_block();
     const int variant = P.variant[form] > 0 ? P.variant[form] : hop_variant();
@@ -153,6 +160,19 @@ cudaError_t Ops<T>::hop(int recon, int epi, int red, const HopParams& P, cudaStr
     WD_HOP_CASE(18, EPI_YZ, RED_NORM)
 #undef WD_HOP_CASE
     return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Ops<T>::apply_mat(int n, int nrhs, long long vs, const uint4* mat, const uint4* in, uint4* out,
+                              cudaStream_t s) {
+    k_apply_mat<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, mat, in, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::mat_from64(int n, const uint4* src64, uint4* dst, cudaStream_t s) {
+    k_mat_from64<T><<<stream_blocks(n, VEC_BLOCK), VEC_BLOCK, 0, s>>>(n, src64, dst);
+    return cudaGetLastError();
 }
 
 template <typename T>

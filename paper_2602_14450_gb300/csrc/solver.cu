@@ -71,6 +71,8 @@ struct Sys {
     uint4 *phat = nullptr, *shat = nullptr, *PHI = nullptr;            // M p, M s, fields of the collapsed M
     const float2* V = nullptr;                                         // collapsed preconditioner weights
     int* err = nullptr;                                                // raised by a bounded wait that gave up
+    // clover blocks (null without a clover term): C^-1 in FP64 and in the inner precision, C in FP64
+    const uint4 *mi64e = nullptr, *mi64o = nullptr, *mf64e = nullptr, *mf64o = nullptr, *mie = nullptr, *mio = nullptr;
     std::vector<double> eta_norm;
     std::vector<bool> active;
 };
@@ -85,6 +87,12 @@ static int prepare(Sys& S, int prec, int recon_lo, bool learned) {
     if (rc != WD_OK) return rc;
     if ((rc = ensure_links(h, WD_FP64, 18, &S.le64, &S.lo64)) != WD_OK) return rc;
     if ((rc = ensure_links(h, prec, recon_lo, &S.le, &S.lo)) != WD_OK) return rc;
+    if (h->have_clover) {
+        if (learned) return fail(h, WD_ERR_INVALID_ARG, "learned scheme: not available with a clover term");
+        if ((rc = ensure_clover(h, WD_FP64, 0, &S.mi64e, &S.mi64o)) != WD_OK) return rc;
+        if ((rc = ensure_clover(h, WD_FP64, 1, &S.mf64e, &S.mf64o)) != WD_OK) return rc;
+        if ((rc = ensure_clover(h, prec, 0, &S.mie, &S.mio)) != WD_OK) return rc;
+    }
     const size_t b64 = vec_bytes(h, WD_FP64) * S.nrhs, blo = vec_bytes(h, prec) * S.nrhs;
     S.vs64 = (long long)spinor_units(WD_FP64) * h->g.Vh;
     S.vs = (long long)spinor_units(prec) * h->g.Vh;
@@ -138,9 +146,10 @@ static HopParams hop_params(const Sys& S, int stage, int guard_kind) {
 // One FP64 hop over all right-hand sides of a system.
 static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, int epi, int red, double a,
                          const uint4* y, double b, const uint4* z, double c, int stage, int guard_kind,
-                         cudaStream_t s) {
+                         cudaStream_t s, const uint4* mat = nullptr) {
     HopParams P = hop_params(S, stage, guard_kind);
     apply_tuning(S.h, WD_FP64, 18, P);
+    P.mat = mat;
     P.vs = S.vs64;
     P.parity = parity;
     P.links = parity == 0 ? S.le64 : S.lo64;
@@ -178,9 +187,9 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
             pa = S.phat;
         }
         // v = A p = p - kappa^2 H_eo H_oe p ; alpha = rho / (r*, v)
-        P.parity = 1; P.links = S.lo; P.in = pa; P.out = S.tmp; P.a = 1.0;
+        P.parity = 1; P.links = S.lo; P.in = pa; P.out = S.tmp; P.a = 1.0; P.mat = S.mio;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.v; P.y = pa; P.a = -k2; P.b = 1.0;
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.v; P.y = pa; P.a = -k2; P.b = 1.0; P.mat = S.mie;
         P.rstar = S.rs; P.rc = red_ctx(h, ST_ALPHA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_RSV, P, s)) != cudaSuccess) return e;
         // r := r - alpha v
@@ -193,9 +202,9 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         // t = A s ; omega from (t, s), (t, t), (s, s)
         P.rc = red_ctx(h, ST_NONE);
         P.parity = 1; P.links = S.lo; P.in = sa; P.out = S.tmp; P.y = nullptr; P.a = 1.0; P.b = 0.0;
-        P.rstar = nullptr;
+        P.rstar = nullptr; P.mat = S.mio;
         if ((e = Ops<T>::hop(recon, EPI_H, RED_NONE, P, s)) != cudaSuccess) return e;
-        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.t; P.y = sa; P.a = -k2; P.b = 1.0;
+        P.parity = 0; P.links = S.le; P.in = S.tmp; P.out = S.t; P.y = sa; P.a = -k2; P.b = 1.0; P.mat = S.mie;
         P.rstar = learned ? S.r : nullptr;   // dot partner s when t = A M s
         P.rc = red_ctx(h, ST_OMEGA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_TS, P, s)) != cudaSuccess) return e;
@@ -317,17 +326,25 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         WD_CUDA(h, cudaMemcpyAsync(h->st, h->hst, sizeof(SolverState) * S.nrhs, cudaMemcpyHostToDevice, s));
         WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_e, red_ctx(h, ST_ACC_SET), GUARD_NONE, s));
         WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_o, red_ctx(h, ST_ACC), GUARD_NONE, s));
-        WD_CUDA(h, hop64(S, 0, S.eta_o, S.bhat, EPI_Y, RED_NONE, h->kappa, S.eta_e, 1.0, nullptr, 0.0, ST_NONE,
-                         GUARD_NONE, s));
+        if (S.mi64e) {   // b^ = C_ee^-1 (eta_e + kappa H_eo C_oo^-1 eta_o)
+            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.tmp64, s));
+            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64e, S.eta_e, S.bhat, s));
+            WD_CUDA(h, hop64(S, 0, S.tmp64, S.bhat, EPI_Y, RED_NONE, h->kappa, S.bhat, 1.0, nullptr, 0.0, ST_NONE,
+                             GUARD_NONE, s, S.mi64e));
+            nk += 2;
+        } else {
+            WD_CUDA(h, hop64(S, 0, S.eta_o, S.bhat, EPI_Y, RED_NONE, h->kappa, S.eta_e, 1.0, nullptr, 0.0, ST_NONE,
+                             GUARD_NONE, s));
+        }
         nk += 2 * S.nrhs + 3;
         if (prm.x_is_guess) {
             if (!S.x_dev) WD_CUDA(h, cudaMemcpyAsync(S.xl, S.x, lexb, cudaMemcpyHostToDevice, s));
             for (int r = 0; r < S.nrhs; ++r)
                 WD_CUDA(h, Ops<double>::pack(h->g, 0, S.xl + r * len, S.x64 + r * S.vs64, s));
             WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE,
-                             GUARD_NONE, s));
+                             GUARD_NONE, s, S.mi64o));
             WD_CUDA(h, hop64(S, 0, S.tmp64, S.r64, EPI_YZ, RED_NORM, h->kappa * h->kappa, S.bhat, 1.0, S.x64, -1.0,
-                             ST_OUTER, GUARD_NONE, s));
+                             ST_OUTER, GUARD_NONE, s, S.mi64e));
             nk += S.nrhs + 2;
         } else {
             WD_CUDA(h, cudaMemsetAsync(S.x64, 0, vec_bytes(h, WD_FP64) * S.nrhs, s));
@@ -393,7 +410,9 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                 if (trips == 0) S.eta_norm[r] = std::sqrt(q.acc);
                 const double rn = q.rnorm, en = S.eta_norm[r];
                 out[k].outer_residual = en > 0 ? rn / en : 0.0;
-                bool act = (rn > tol * en) && status[k] == WD_OK;
+                // with clover blocks |eta - D xi| = |C_ee (b^ - A xi_e)| <= clover_bound |b^ - A xi_e|
+                const double tol_eo = tol / clover_bound(S.h);
+                bool act = (rn > tol_eo * en) && status[k] == WD_OK;
                 if (act && !std::isfinite(rn)) {
                     status[k] = WD_ERR_NONFINITE;
                     act = false;
@@ -425,7 +444,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                     q.hist_cap = hist_on ? hist_iters : 0;
                     q.max_matvecs = prm.max_inner;
                     // FP64 BiCGStab: one inner solve to the outer tolerance; mixed: eps of Table 2
-                    q.eps = cfg.fp64_inner ? std::max(0.5 * tol * en / rn, 1e-15) : prm.inner_eps;
+                    q.eps = cfg.fp64_inner ? std::max(0.5 * tol_eo * en / rn, 1e-15) : prm.inner_eps;
                     q.done = 0;
                 }
             }
@@ -464,9 +483,9 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             });
             WD_CUDA(h, e);
             WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE,
-                             GUARD_OUTER, s));
+                             GUARD_OUTER, s, S.mi64o));
             WD_CUDA(h, hop64(S, 0, S.tmp64, S.r64, EPI_YZ, RED_NORM, h->kappa * h->kappa, S.bhat, 1.0, S.x64, -1.0,
-                             ST_OUTER, GUARD_OUTER, s));
+                             ST_OUTER, GUARD_OUTER, s, S.mi64e));
             nk += 3;
         }
         if ((rc = read_states(sys, s)) != WD_OK) return rc;
@@ -506,11 +525,26 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         wd_handle* h = S.h;
         const double kap = h->kappa;
         const size_t len = (size_t)2 * h->g.Vh * 24;
-        WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.eta_o, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE, s));
-        WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.x64, -1.0, ST_ACC_SET,
-                         GUARD_NONE, s));
-        WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.xo, -1.0, ST_ACC, GUARD_NONE,
-                         s));
+        if (S.mi64o) {   // xi_o = C_oo^-1 (eta_o + kappa H_oe xi_e); residual eta - (C xi - kappa H xi)
+            const int nv = h->g.Vh;
+            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.xo, s));
+            WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.xo, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE, s,
+                             S.mi64o));
+            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mf64e, S.x64, S.r64, s));
+            WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.r64, -1.0, ST_ACC_SET,
+                             GUARD_NONE, s));
+            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mf64o, S.xo, S.tmp64, s));
+            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.tmp64, -1.0, ST_ACC,
+                             GUARD_NONE, s));
+            nk += 3;
+        } else {
+            WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.eta_o, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE,
+                             s));
+            WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.x64, -1.0, ST_ACC_SET,
+                             GUARD_NONE, s));
+            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.xo, -1.0, ST_ACC,
+                             GUARD_NONE, s));
+        }
         for (int r = 0; r < S.nrhs; ++r) {
             WD_CUDA(h, Ops<double>::unpack(h->g, 0, S.x64 + r * S.vs64, S.xl + r * len, s));
             WD_CUDA(h, Ops<double>::unpack(h->g, 1, S.xo + r * S.vs64, S.xl + r * len, s));

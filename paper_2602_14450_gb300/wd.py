@@ -27,7 +27,7 @@ SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_pla
           "mixed_fp16": WD_MIXED_FP16, "mixed_bf16": WD_MIXED_BF16}
 
 # Exported symbols (the declarations of include/wd.h).
-SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_vector_bytes", "wd_pack",
+SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_set_clover", "wd_vector_bytes", "wd_pack",
            "wd_unpack", "wd_apply", "wd_apply_eo_noalloc", "wd_tune", "wd_solve_params_default", "wd_solve",
            "wd_solve_batch",
            "wd_precond_set",
@@ -78,6 +78,7 @@ def lib():
         L.wd_destroy.argtypes = [vp]
         L.wd_set_gauge.argtypes = [vp, vp, i]
         L.wd_gauge_unitarity.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        L.wd_set_clover.argtypes = [vp, d]
         L.wd_vector_bytes.argtypes = [vp, i]
         L.wd_vector_bytes.restype = sz
         L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
@@ -162,6 +163,10 @@ class Lattice:
         """u: float64 tensor in the host layout [4, V, 3, 3, 2] (CPU or CUDA)."""
         where = WD_DEVICE if u.is_cuda else WD_HOST
         self._check(lib().wd_set_gauge(self.h, _ptr(u.contiguous()), where), "wd_set_gauge")
+
+    def set_clover(self, csw):
+        """wd_set_clover: add the clover term with coefficient csw (0 removes it)."""
+        self._check(lib().wd_set_clover(self.h, float(csw)), "wd_set_clover")
 
     def unitarity(self):
         a, b = C.c_double(), C.c_double()
