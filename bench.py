@@ -292,6 +292,7 @@ def main():
         studies_out["learned"] = studies.learned_preconditioner(wl.kappa, lat, b, TOL, stream)
         studies_out["tableau"] = studies.tableau(workloads.KAPPA["16x16x16x32"], TOL, stream)
         studies_out["table2"] = studies.table2(lat, 1e-13, stream)
+        studies_out["clover"] = studies.clover(wl, 1.0, TOL, stream)
 
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -209,3 +209,35 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
     lat.close()
     return out
 
+
+
+def clover(wl, csw: float = 1.0, tol: float = 1e-10, stream=None) -> dict:
+    """The clover matrix (wd_set_clover) on a workload: FP16-mixed (Alg. 2 + 3)
+    against FP64 time to tol, with the Wilson-only solves of the same system
+    beside them, and the clover FP16 hop with its C^-1 block (EO operator)."""
+    stream = stream or torch.cuda.current_stream()
+    lat = wd.Lattice(wl.dims, wl.kappa)
+    lat.set_gauge(torch.view_as_real(wl.gauge()).contiguous())
+    b = synth.to_host_layout(wl.source()).cuda()
+    x = torch.zeros_like(b)
+    out = {"csw": csw, "kappa": wl.kappa}
+    for name, c in (("wilson", 0.0), ("clover", csw)):
+        lat.set_clover(c)
+        row = {}
+        for scheme in ("mixed_fp16", "fp64"):
+            lat.solve(b, x.zero_(), tol, scheme, stream=stream, check=False)
+            st, t = _timed(lambda: lat.solve(b, x.zero_(), tol, scheme, stream=stream, check=False), stream)
+            row[scheme] = {"time_s": t, "matvecs": st.inner_matvecs, "outer": st.outer_iterations,
+                           "status": st.status, "true_residual": st.true_residual}
+        row["speedup_fp16_vs_fp64"] = row["fp64"]["time_s"] / row["mixed_fp16"]["time_s"]
+        nb = lat.vector_bytes("fp16")
+        src = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        dst = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        src.view(torch.float16).normal_()
+        for _ in range(3):
+            lat.apply("fp16", 12, wd.WD_OP_EO_A, src, dst, stream)
+        _, t = _timed(lambda: [lat.apply("fp16", 12, wd.WD_OP_EO_A, src, dst, stream) for _ in range(20)], stream)
+        row["eo_operator_fp16_us"] = t / 20 * 1e6
+        out[name] = row
+    lat.close()
+    return out
