@@ -284,6 +284,65 @@ __global__ void __launch_bounds__(256) k_mat_from64(int n, const uint4* src, uin
     }
 }
 
+// out = M in site by site with M in the chiral packing
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_chiral(int n, int nrhs, long long vs, const uint4* mat,
+                                                      const uint4* in, uint4* out) {
+    typedef typename Unit<T>::C C;
+    const Slice sl = slice_of(nrhs);
+    in += sl.rhs * vs;
+    out += sl.rhs * vs;
+    RHS_LOOP(h, n) {
+        C v[24], o[24];
+        load_spinor<T>(in, n, h, v);
+        mat_mul_chiral<T>(mat, n, h, v, o);
+        store_spinor<T>(out, n, h, o);
+    }
+}
+
+// Chiral packing of full FP64 blocks M (144 complex per site, element (i, j)
+// in unit 12 i + j): S_-/+ (k a, k' b) = (M[k a][k' b] -/+ M[k a][k'+2 b]
+// -/+ M[k+2 a][k' b] + M[k+2 a][k'+2 b]) / 4 with spin-colour index 3 s + a,
+// stored as described at mat_mul_chiral (block + first).
+template <typename T>
+__global__ void __launch_bounds__(128) k_chiral_from64(int n, const uint4* src, uint4* dst) {
+    typedef typename Unit<T>::C C;
+    constexpr int N = Unit<T>::N;
+    GRID_STRIDE(h, n) {
+        for (int c = 0; c < 2; ++c) {
+            const double sg = c == 0 ? -1.0 : 1.0;
+            double blk[40];
+            for (int i = 0; i < 40; ++i) blk[i] = 0.0;
+            int q = 6;
+            for (int i = 0; i < 6; ++i)
+                for (int j = i; j < 6; ++j) {
+                    const int k = i / 3, a = i % 3, kk = j / 3, b = j % 3;
+                    const int r0 = 3 * k + a, r2 = 3 * (k + 2) + a, c0 = 3 * kk + b, c2 = 3 * (kk + 2) + b;
+                    double re = 0.0, im = 0.0;
+                    const int idx[4] = {12 * r0 + c0, 12 * r0 + c2, 12 * r2 + c0, 12 * r2 + c2};
+                    const double f[4] = {1.0, sg, sg, 1.0};
+                    for (int t = 0; t < 4; ++t) {
+                        const uint4 w = src[(size_t)idx[t] * n + h];
+                        re += f[t] * Unit<double>::get(w, 0);
+                        im += f[t] * Unit<double>::get(w, 1);
+                    }
+                    if (i == j) {
+                        blk[i] = 0.25 * re;
+                    } else {
+                        blk[q] = 0.25 * re;
+                        blk[q + 1] = 0.25 * im;
+                        q += 2;
+                    }
+                }
+            for (int u = 0; u < 40 / N; ++u) {
+                C v[N];
+                for (int e = 0; e < N; ++e) v[e] = (C)blk[u * N + e];
+                dst[(size_t)(c * (40 / N) + u) * n + h] = Unit<T>::put(v);
+            }
+        }
+    }
+}
+
 // x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 2 correction; Alg. 1: s^ -> s)
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(int n, int nrhs, long long vs, long long vs64, uint4* x64,

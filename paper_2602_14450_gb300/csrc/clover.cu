@@ -7,7 +7,9 @@
 // traversed mu-then-nu. Built once per gauge field in FP64, one thread per
 // site: C and C^{-1} (Gauss-Jordan with partial pivoting) are written as
 // 12 x 12 complex blocks (row-major, spin-colour index 3 s + a) per parity in
-// the unit layout of the spinors; lower precisions are converted on first use.
+// the unit layout of the spinors. The operators use C^-1 in the chiral packing
+// (two Hermitian 6 x 6 blocks, 80 reals per site; see mat_mul_chiral), made
+// on first use per precision; C itself (full) serves the true residual.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -220,8 +222,8 @@ int clover_build(wd_handle* h) {
     if (hs) return fail(h, WD_ERR_INVALID_ARG, "wd_set_clover: a clover block is singular");
     for (int k = 0; k < 2; ++k)
         for (int p = 0; p < 4; ++p) h->clov[k][p][0] = h->clov[k][p][1] = nullptr;
-    h->clov[0][WD_FP64][0] = b[2];
-    h->clov[0][WD_FP64][1] = b[3];
+    h->clov_inv64[0] = b[2];
+    h->clov_inv64[1] = b[3];
     h->clov[1][WD_FP64][0] = b[0];
     h->clov[1][WD_FP64][1] = b[1];
     h->gen += 1;
@@ -235,15 +237,18 @@ int ensure_clover(wd_handle* h, int prec, int kind, const uint4** even, const ui
     if (!h->have_clover) return WD_OK;
     for (int p = 0; p < 2; ++p) {
         if (!h->clov[kind][prec][p]) {
-            const size_t units = (size_t)288 / (16 / (prec == WD_FP64 ? 8 : prec == WD_FP32 ? 4 : 2));
+            // C^-1: chiral packing, 80 reals per site; C: full block, 288 reals per site
+            const size_t per_unit = 16 / (prec == WD_FP64 ? 8 : prec == WD_FP32 ? 4 : 2);
+            const size_t units = (kind == 0 ? 80 : 288) / per_unit;
             const std::string name = "clov.k" + std::to_string(kind) + ".p" + std::to_string(prec) + "." +
                                      std::to_string(p);
             uint4* dst = (uint4*)workspace(h, name, (size_t)h->g.Vh * units * 16);
             if (!dst) return fail(h, WD_ERR_CUDA, "out of device memory (clover blocks)");
-            const uint4* src = h->clov[kind][WD_FP64][p];
+            const uint4* src = kind == 0 ? h->clov_inv64[p] : h->clov[1][WD_FP64][p];
             cudaError_t e = by_prec(prec, [&](auto tag) {
                 typedef typename decltype(tag)::type T;
-                return Ops<T>::mat_from64(h->g.Vh, src, dst, nullptr);
+                return kind == 0 ? Ops<T>::chiral_from64(h->g.Vh, src, dst, nullptr)
+                                 : Ops<T>::mat_from64(h->g.Vh, src, dst, nullptr);
             });
             WD_CUDA(h, e);
             WD_CUDA(h, cudaDeviceSynchronize());
@@ -268,6 +273,7 @@ extern "C" int wd_set_clover(wd_handle* h, double csw) {
         h->csw = 0.0;
         for (int k = 0; k < 2; ++k)
             for (int p = 0; p < 4; ++p) h->clov[k][p][0] = h->clov[k][p][1] = nullptr;
+        h->clov_inv64[0] = h->clov_inv64[1] = nullptr;
         h->gen += 1;
         return WD_OK;
     }

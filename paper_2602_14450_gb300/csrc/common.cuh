@@ -179,6 +179,67 @@ __device__ __forceinline__ void mat_mul(const uint4* __restrict__ mat, int strid
     }
 }
 
+// Clover blocks commute with gamma_5 = -[[0, 1], [1, 0]] (spin blocks of this
+// basis), so in the chiral combinations chi_+/- = psi_{0,1} -/+ psi_{2,3} of
+// the spin pairs they split into two Hermitian 6 x 6 blocks S_+, S_-. Stored
+// per site: for c = +, - the real diagonal (6 reals), the upper triangle
+// (i < j, row by row: 15 complex) and 4 zeros, 40 reals per block and 80 per
+// site (units of 16 bytes as for spinors). With S = T' M T'^T / 4 (T' the
+// unnormalised chiral map), M v = T'^T S T' v:
+//   out_{0,1} = o_+ + o_-,  out_{2,3} = o_- - o_+,  o_c = S_c chi_c.
+template <typename T>
+__device__ __forceinline__ void chiral_block_mul(const uint4* __restrict__ mat, int stride, int h, int unit0,
+                                                 const typename Unit<T>::C (&x)[12], typename Unit<T>::C (&o)[12]) {
+    typedef typename Unit<T>::C C;
+    constexpr int N = Unit<T>::N;
+    constexpr int UB = 40 / N;   // units per block
+    C m[40];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const uint4 w = __ldg(mat + (size_t)(unit0 + u) * stride + h);
+#pragma unroll
+        for (int i = 0; i < N; ++i) m[u * N + i] = Unit<T>::get(w, i);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        o[2 * i] = m[i] * x[2 * i];
+        o[2 * i + 1] = m[i] * x[2 * i + 1];
+    }
+    int q = 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+            const C br = m[q], bi = m[q + 1];
+            q += 2;
+            // o_i += b x_j ; o_j += conj(b) x_i
+            o[2 * i] = fma(br, x[2 * j], fma(-bi, x[2 * j + 1], o[2 * i]));
+            o[2 * i + 1] = fma(br, x[2 * j + 1], fma(bi, x[2 * j], o[2 * i + 1]));
+            o[2 * j] = fma(br, x[2 * i], fma(bi, x[2 * i + 1], o[2 * j]));
+            o[2 * j + 1] = fma(br, x[2 * i + 1], fma(-bi, x[2 * i], o[2 * j + 1]));
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void mat_mul_chiral(const uint4* __restrict__ mat, int stride, int h,
+                                               const typename Unit<T>::C (&v)[24], typename Unit<T>::C (&out)[24]) {
+    typedef typename Unit<T>::C C;
+    constexpr int UB = 40 / Unit<T>::N;
+    C xp[12], xm[12], op[12], om[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {   // spin pair (k, k + 2), colour: reals 6 k + 2 a + re/im
+        xp[i] = v[i] - v[12 + i];
+        xm[i] = v[i] + v[12 + i];
+    }
+    chiral_block_mul<T>(mat, stride, h, 0, xp, op);
+    chiral_block_mul<T>(mat, stride, h, UB, xm, om);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        out[i] = op[i] + om[i];
+        out[12 + i] = om[i] - op[i];
+    }
+}
+
 // --------------------------------------------------------------- geometry ---
 
 // Division of a non-negative int below 2^31 by a fixed divisor d in

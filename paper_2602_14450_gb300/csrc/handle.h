@@ -59,7 +59,8 @@ struct wd_handle {
 
     double csw = 0.0;                  // clover coefficient of wd_set_clover (0: plain Wilson)
     bool have_clover = false;
-    uint4* clov[2][4][2] = {};         // clover blocks [C^-1, C][prec][parity], built on first use
+    uint4* clov[2][4][2] = {};         // clover blocks [C^-1 (chiral packing), C (full)][prec][parity], on first use
+    uint4* clov_inv64[2] = {};         // full FP64 C^-1 per parity, the source of the chiral packings
 
     // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1][without / with fused reduction]; 0 = default
     int tune_variant[4][2][2] = {};

@@ -219,9 +219,9 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& P, uint4* vout, co
     constexpr int NS = RedSums<RED>::N;
     const int Vh = P.g.Vh;
     const C ca = (C)P.a, cb = (C)P.b, cc = (C)P.c;
-    if constexpr (MAT) {   // the site-local block (clover, Eqs. 4-5) applied to the hop
+    if constexpr (MAT) {   // the site-local block (clover C^-1, Eqs. 4-5, chiral packing) applied to the hop
         C t[24];
-        mat_mul<T>(P.mat, Vh, h, acc, t);
+        mat_mul_chiral<T>(P.mat, Vh, h, acc, t);
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] = t[i];
     }

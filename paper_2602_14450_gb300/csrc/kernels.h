@@ -31,8 +31,8 @@ struct HopParams {
     const SolverState* guard;  // per-rhs state consulted by the guard
     int guard_kind;            // GuardKind
     int* err;                  // set to 1 by a kernel whose bounded wait gave up (may be null)
-    const uint4* mat;          // site-local 12 x 12 complex block of the output parity applied to the
-                               // hop: out = M (a H in) + b y + c z; null = none (storage T)
+    const uint4* mat;          // site-local 12 x 12 complex block of the output parity (chiral packing,
+                               // storage T) applied to the hop: out = M (a H in) + b y + c z; null = none
     int variant[2];            // kernel variant (hop_variant() numbering) without / with a fused
                                // reduction; 0 = the process default
     int block[2];              // threads per block, likewise; 0 = the process default
@@ -72,6 +72,11 @@ template <typename T> struct Ops {
                                  cudaStream_t s);
     // blocks of storage T from FP64 blocks (288 reals per site, n sites)
     static cudaError_t mat_from64(int n, const uint4* src64, uint4* dst, cudaStream_t s);
+    // out = M in with M in the chiral packing (80 reals per site, see mat_mul_chiral)
+    static cudaError_t apply_chiral(int n, int nrhs, long long vs, const uint4* mat, const uint4* in, uint4* out,
+                                    cudaStream_t s);
+    // chiral packing in storage T from full FP64 blocks that commute with gamma_5
+    static cudaError_t chiral_from64(int n, const uint4* src64, uint4* dst, cudaStream_t s);
     static cudaError_t pack(const Geom& g, int parity, const double* lex, uint4* out, cudaStream_t s);
     static cudaError_t unpack(const Geom& g, int parity, const uint4* in, double* lex, cudaStream_t s);
     static cudaError_t build_links(int recon, const Geom& g, int parity, const double* U, uint4* out, cudaStream_t s);

@@ -170,6 +170,19 @@ cudaError_t Ops<T>::apply_mat(int n, int nrhs, long long vs, const uint4* mat, c
 }
 
 template <typename T>
+cudaError_t Ops<T>::apply_chiral(int n, int nrhs, long long vs, const uint4* mat, const uint4* in, uint4* out,
+                                 cudaStream_t s) {
+    k_apply_chiral<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, mat, in, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::chiral_from64(int n, const uint4* src64, uint4* dst, cudaStream_t s) {
+    k_chiral_from64<T><<<stream_blocks(n, 128), 128, 0, s>>>(n, src64, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Ops<T>::mat_from64(int n, const uint4* src64, uint4* dst, cudaStream_t s) {
     k_mat_from64<T><<<stream_blocks(n, VEC_BLOCK), VEC_BLOCK, 0, s>>>(n, src64, dst);
     return cudaGetLastError();

@@ -327,8 +327,8 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_e, red_ctx(h, ST_ACC_SET), GUARD_NONE, s));
         WD_CUDA(h, Ops<double>::norm2(nv, S.nrhs, S.vs64, S.eta_o, red_ctx(h, ST_ACC), GUARD_NONE, s));
         if (S.mi64e) {   // b^ = C_ee^-1 (eta_e + kappa H_eo C_oo^-1 eta_o)
-            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.tmp64, s));
-            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64e, S.eta_e, S.bhat, s));
+            WD_CUDA(h, Ops<double>::apply_chiral(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.tmp64, s));
+            WD_CUDA(h, Ops<double>::apply_chiral(nv, S.nrhs, S.vs64, S.mi64e, S.eta_e, S.bhat, s));
             WD_CUDA(h, hop64(S, 0, S.tmp64, S.bhat, EPI_Y, RED_NONE, h->kappa, S.bhat, 1.0, nullptr, 0.0, ST_NONE,
                              GUARD_NONE, s, S.mi64e));
             nk += 2;
@@ -527,7 +527,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         const size_t len = (size_t)2 * h->g.Vh * 24;
         if (S.mi64o) {   // xi_o = C_oo^-1 (eta_o + kappa H_oe xi_e); residual eta - (C xi - kappa H xi)
             const int nv = h->g.Vh;
-            WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.xo, s));
+            WD_CUDA(h, Ops<double>::apply_chiral(nv, S.nrhs, S.vs64, S.mi64o, S.eta_o, S.xo, s));
             WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.xo, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE, s,
                              S.mi64o));
             WD_CUDA(h, Ops<double>::apply_mat(nv, S.nrhs, S.vs64, S.mf64e, S.x64, S.r64, s));
