@@ -3,7 +3,11 @@
 32^3 x 64 with the mixed FP16/FP64 solver (Alg. 2 + Alg. 3), beside the pure
 FP64 and FP32-mixed forms, and the FP16 Dslash against the HBM roofline.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--arith 16|32]
+
+--arith picks the arithmetic of the FP16 stencil (wd_set_arith): 16, the
+default, is the paper's FP16 arithmetic (Sec. 5); 32 widens to FP32. The other
+one is reported among the forms.
 
 One step = one full solve (even-odd source, refinement with FP16 inner
 BiCGStab, odd reconstruction, FP64 true residual) of a synthetic workload
@@ -24,9 +28,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one launch of the FP16 12-real hop at 32^3 x 64,
-# from the ncu capture summarised in profiles/hop_fp16_12_32x32x32x64.md; set
-# to None whenever that kernel changes until it is captured again.
-HOP_FP16_12_TRAFFIC = 269_941_248
+# from the ncu captures summarised in profiles/ (hop_fp16_12_32x32x32x64.md for
+# FP32 arithmetic, hop16_fp16_12_32x32x32x64.md for FP16 arithmetic); set to
+# None whenever that kernel changes until it is captured again.
+HOP_FP16_12_TRAFFIC = {32: 269_941_248, 16: None}
 
 METRIC = "time to ‖r‖/‖b‖≤1e-10 at 32^3×64, FP16-mixed vs FP64; Dslash GB/s vs HBM peak"
 TOL = 1e-10
@@ -44,6 +49,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and FP32-mixed solves")
     ap.add_argument("--no-studies", action="store_true", help="skip the batched and learned-preconditioner sections")
     ap.add_argument("--no-tune", action="store_true", help="keep the default hop kernel configuration")
+    ap.add_argument("--arith", type=int, default=16, choices=[16, 32],
+                    help="arithmetic of the FP16 stencil of the headline solve (wd_set_arith)")
     return ap.parse_args()
 
 
@@ -218,6 +225,8 @@ def main():
     # the library's autotuner picks the hop kernel variant and block size for the inner and outer precisions
     tuning = {} if args.no_tune else {f"{p}_{r}": lat.tune(p, r, 1, stream)
                                       for p, r in (("fp16", 12), ("fp64", 18), ("fp32", 12))}
+    lat.set_arith(args.arith)
+    other = 48 - args.arith
 
     for _ in range(args.warmup):
         st = lat.solve(b, x, TOL, "mixed_fp16", prm, stream)
@@ -255,7 +264,11 @@ def main():
     forms = {"mixed_fp16": {"time_s": ms / 1e3, "inner_matvecs": st.inner_matvecs,
                             "outer_iterations": st.outer_iterations, "true_residual": st.true_residual}}
     if not args.no_forms:
-        for scheme in ("mixed_fp32", "fp64", "mixed_bf16", "mixed_fp16_plain"):
+        for name in ("mixed_fp32", "fp64", "mixed_bf16", "mixed_fp16_plain", f"mixed_fp16_arith{other}"):
+            scheme = name
+            if name.startswith("mixed_fp16_arith"):        # the headline solve with the other stencil arithmetic
+                scheme = "mixed_fp16"
+                lat.set_arith(other)
             p = wd.default_params(scheme)
             if scheme == "mixed_fp16_plain":   # unrescaled FP16 (Alg. 1) crawls: bound its work
                 p.max_inner, p.max_outer = 2000, 10
@@ -269,39 +282,45 @@ def main():
             s2 = lat.solve(b, xs, TOL, scheme, p, stream, check=False)
             f1.record(stream)
             torch.cuda.synchronize()
-            forms[scheme] = {"time_s": f0.elapsed_time(f1) / 1e3, "inner_matvecs": s2.inner_matvecs,
-                             "outer_iterations": s2.outer_iterations, "true_residual": s2.true_residual,
-                             "status": s2.status}
+            forms[name] = {
+                "time_s": f0.elapsed_time(f1) / 1e3, "inner_matvecs": s2.inner_matvecs,
+                "outer_iterations": s2.outer_iterations, "true_residual": s2.true_residual, "status": s2.status}
+            lat.set_arith(args.arith)
 
     # Dslash: the dominant kernel of the inner solve, timed alone on the launching stream
     sweep = {}
-    for prec, recon in (("fp16", 12), ("fp16", 18), ("fp32", 12), ("fp32", 18), ("fp64", 18)):
+    for prec, recon in (("fp16", 12), ("fp16", 18), ("fp16a", 12), ("fp16a", 18), ("fp32", 12), ("fp32", 18),
+                        ("fp64", 18)):
         sweep[f"{prec}_{recon}"] = dslash_bench.hop_timing(lat, prec, recon, args.dslash_launches, stream)
     peak, peak_kind = measured_peaks()
-    top = sweep["fp16_12"]
+    top = sweep["fp16a_12" if args.arith == 16 else "fp16_12"]
     roof = {"bound": "hbm", "achieved": top["gbs"], "peak": peak, "unit": "GB/s", "frac": top["gbs"] / peak,
-            "traffic": HOP_FP16_12_TRAFFIC if wl.dims == (32, 32, 32, 64) else None,
-            "kernel": "hop_kernel<__half,12,EPI_H,RED_NONE> (H_eo, FP16, 12-real links)",
+            "traffic": HOP_FP16_12_TRAFFIC[args.arith] if wl.dims == (32, 32, 32, 64) else None,
+            "kernel": ("hop16_kernel<12,EPI_H,RED_NONE> (H_eo, FP16 storage and arithmetic, 12-real links)"
+                       if args.arith == 16 else
+                       "hop_kernel<__half,12,EPI_H,RED_NONE> (H_eo, FP16 storage, FP32 arithmetic, 12-real links)"),
             "peak_kind": peak_kind, "bytes_per_site": top["bytes_per_site"], "sites_per_launch": vh,
             "avg_launch_us": top["us"]}
 
     studies_out = {}
     if not args.no_studies:
         from paper_2602_14450_gb300 import studies
-        studies_out["batched"] = studies.batched(workloads.KAPPA["16x16x16x32"], TOL, stream)
+        studies_out["batched"] = studies.batched(workloads.KAPPA["16x16x16x32"], TOL, stream, args.arith)
         studies_out["learned"] = studies.learned_preconditioner(wl.kappa, lat, b, TOL, stream)
-        studies_out["tableau"] = studies.tableau(workloads.KAPPA["16x16x16x32"], TOL, stream)
+        studies_out["tableau"] = studies.tableau(workloads.KAPPA["16x16x16x32"], TOL, stream, arith=args.arith)
         studies_out["table2"] = studies.table2(lat, 1e-13, stream)
-        studies_out["clover"] = studies.clover(wl, 1.0, TOL, stream)
+        studies_out["clover"] = studies.clover(wl, 1.0, TOL, stream, args.arith)
 
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f16 storage / f32 arithmetic / f64 refinement", "data": "synthetic",
+        "dtype": (f"f16 storage / f{args.arith} stencil arithmetic, f32 vector arithmetic / f64 refinement"),
+        "data": "synthetic",
         "config": {"workload": f"wilson_eo_{args.workload}", "lattice": list(wl.dims), "kappa": wl.kappa,
                    "links": "exp(i 0.5 H) + 3 APE steps (alpha 0.5), SU(3)-reprojected; FP16 12-real in the inner solve",
                    "source": f"Gaussian, seed {wl.source_seed}", "tol": TOL,
                    "scheme": "Alg. 2 + Alg. 3 (s=128, sigma=64, recalculated gamma, eps^2=1e-4)",
+                   "stencil_arith_bits": args.arith,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": bh.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8},
         "gpu_launches": launches,

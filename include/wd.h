@@ -179,6 +179,20 @@ int wd_gauge_unitarity(wd_handle* h, double* max_unitarity_dev, double* max_det_
  * c_sw or a singular block. */
 int wd_set_clover(wd_handle* h, double csw);
 
+/* Arithmetic of the hopping term H on FP16 storage (Sec. 5): bits = 32 (the
+ * default) widens the stored FP16 values and computes the projection's
+ * products, the SU(3) multiplies and the sum over the eight directions in
+ * FP32; bits = 16 computes all of them in FP16 (packed half2 operations, one
+ * rounding per operation), the arithmetic of the paper's _Float16 build. The
+ * epilogue of a fused kernel (out = a H in + b y + c z, clover blocks, dot
+ * products) stays FP32 and every reduction FP64 in both. Applies to
+ * everything the handle does afterwards with WD_FP16 storage: wd_apply,
+ * wd_apply_eo_noalloc and the inner solves of WD_MIXED_FP16,
+ * WD_MIXED_FP16_PLAIN and WD_MIXED_FP16_LEARNED. WD_ERR_INVALID_ARG for any
+ * other bits. wd_get_arith returns the current setting (0 for a null handle). */
+int wd_set_arith(wd_handle* h, int bits);
+int wd_get_arith(const wd_handle* h);
+
 /* Bytes of one packed parity vector in precision `prec` (24 * V/2 reals). */
 size_t wd_vector_bytes(const wd_handle* h, int prec);
 

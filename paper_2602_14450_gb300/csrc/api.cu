@@ -299,6 +299,19 @@ int wd_gauge_unitarity(wd_handle* h, double* max_unitarity_dev, double* max_det_
     return WD_OK;
 }
 
+int wd_set_arith(wd_handle* h, int bits) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (bits != 16 && bits != 32) return fail(h, WD_ERR_INVALID_ARG, "wd_set_arith: bits must be 16 or 32, got %d", bits);
+    const int a16 = bits == 16 ? 1 : 0;
+    if (a16 != h->arith16) {
+        h->arith16 = a16;
+        h->gen += 1;   // captured solver graphs hold the other kernels
+    }
+    return WD_OK;
+}
+
+int wd_get_arith(const wd_handle* h) { return h ? (h->arith16 ? 16 : 32) : 0; }
+
 size_t wd_vector_bytes(const wd_handle* h, int prec) {
     if (!h || !valid_prec(prec)) return 0;
     return vec_bytes(h, prec);

@@ -65,6 +65,8 @@ struct wd_handle {
     // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1][without / with fused reduction]; 0 = default
     int tune_variant[4][2][2] = {};
     int tune_block[4][2][2] = {};
+
+    int arith16 = 0;                   // wd_set_arith: FP16-storage hops sum in FP16 arithmetic
 };
 
 namespace wd {
@@ -84,12 +86,14 @@ int clover_build(wd_handle* h);
 int ensure_clover(wd_handle* h, int prec, int kind, const uint4** even, const uint4** odd);
 // 1 + 12 |c_sw| kappa bounds the norm of every clover block C.
 inline double clover_bound(const wd_handle* h) { return h->have_clover ? 1.0 + 12.0 * std::fabs(h->csw) * h->kappa : 1.0; }
-// Hop kernel configuration chosen by wd_tune for (prec, recon), if any.
+// Hop kernel configuration chosen by wd_tune for (prec, recon), if any, and
+// the arithmetic of FP16 hops chosen by wd_set_arith.
 inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) {
     for (int f = 0; f < 2; ++f) {
         P.variant[f] = h->tune_variant[prec][recon == 12 ? 0 : 1][f];
         P.block[f] = h->tune_block[prec][recon == 12 ? 0 : 1][f];
     }
+    P.arith16 = (prec == WD_FP16 && h->arith16) ? 1 : 0;
 }
 
 }  // namespace wd

@@ -36,6 +36,7 @@ struct HopParams {
     int variant[2];            // kernel variant (hop_variant() numbering) without / with a fused
                                // reduction; 0 = the process default
     int block[2];              // threads per block, likewise; 0 = the process default
+    int arith16;               // FP16 storage only: 1 = the hopping sum in FP16 arithmetic (hop16_kernel)
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.

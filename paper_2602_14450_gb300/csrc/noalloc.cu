@@ -74,6 +74,7 @@ extern "C" int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void
     P.g = h->g;
     P.nrhs = 1;
     P.guard_kind = GUARD_NONE;
+    P.arith16 = (prec == WD_FP16 && h->arith16) ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
     const double k = h->kappa;
     auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y) {

@@ -8,6 +8,7 @@
 
 #include "blas_impl.cuh"
 #include "hop2_impl.cuh"
+#include "hop16_impl.cuh"
 #include "hop3_impl.cuh"
 #include "hop_impl.cuh"
 #include "kernels.h"
@@ -66,6 +67,21 @@ bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
 
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
+    if constexpr (std::is_same<T, __half>::value) {
+        if (P.arith16) {   // FP16 arithmetic (with or without a site-local block)
+            constexpr int blk = Hop16Bounds<R, D, false>::THREADS;
+            if (P.mat) {
+                const void* km = (const void*)hop16_kernel<R, E, D, true>;
+                const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);
+                hop16_kernel<R, E, D, true><<<nb * P.nrhs, blk, 0, s>>>(P);
+            } else {
+                const void* k = (const void*)hop16_kernel<R, E, D, false>;
+                const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
+                hop16_kernel<R, E, D, false><<<nb * P.nrhs, blk, 0, s>>>(P);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (P.mat) {   // with a site-local block (clover): the one-site-per-thread look-ahead kernel
         const int blk = 128;
         const void* km = (const void*)hop_kernel<T, R, E, D, true, false, true>;

@@ -4,6 +4,8 @@ learned preconditioner M through wd_precond_apply.
     python -m paper_2602_14450_gb300.dslash_bench --dims 32,32,32,64 --cases fp16_12,fp32_18 --launches 50
     python -m paper_2602_14450_gb300.dslash_bench --dims 32,32,32,64 --cases m_fp16 --launches 20
 
+Case "fp16a_R" is FP16 storage with FP16 arithmetic (wd_set_arith(16)).
+
 Links are exp(i 0.5 H) random SU(3) matrices generated on the GPU; inputs
 cycle through four different source vectors so that consecutive launches do
 not find their input in L2 (at 32^3 x 64 every launch streams more than L2
@@ -28,6 +30,15 @@ def bytes_per_site(prec: str, recon: int) -> int:
 
 
 def hop_timing(lat, prec: str, recon: int, launches: int, stream=None) -> dict:
+    if prec == "fp16a":
+        old = lat.arith
+        lat.set_arith(16)
+        try:
+            r = hop_timing(lat, "fp16", recon, launches, stream)
+        finally:
+            lat.set_arith(old)
+        r["case"] = f"fp16a_{recon}"
+        return r
     from . import wd
     vh = lat.vector_bytes(prec) // (24 * BYTES[prec])
     nb = lat.vector_bytes(prec)
@@ -76,7 +87,7 @@ def precond_timing(lat, prec: str, launches: int, stream=None) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", default="32,32,32,64")
-    ap.add_argument("--cases", default="fp16_12,fp16_18,fp32_12,fp32_18,fp64_18,bf16_12")
+    ap.add_argument("--cases", default="fp16_12,fp16_18,fp16a_12,fp16a_18,fp32_12,fp32_18,fp64_18,bf16_12")
     ap.add_argument("--launches", type=int, default=50)
     a = ap.parse_args()
     from . import build, synth, wd

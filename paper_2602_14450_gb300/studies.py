@@ -25,10 +25,11 @@ from . import learned, synth, wd, workloads
 SMEARED_SEED = workloads.GAUGE_SEED
 
 
-def _lattice(dims, kappa, seed):
+def _lattice(dims, kappa, seed, arith=32):
     u = synth.gauge_smeared(dims, seed=seed)
     lat = wd.Lattice(dims, kappa)
     lat.set_gauge(torch.view_as_real(u).contiguous())
+    lat.set_arith(arith)
     return lat
 
 
@@ -48,11 +49,11 @@ def _summary(stats):
             "ok": all(s.status == wd.WD_OK for s in stats)}
 
 
-def batched(kappa: float, tol: float = 1e-10, stream=None) -> dict:
+def batched(kappa: float, tol: float = 1e-10, stream=None, arith: int = 32) -> dict:
     stream = stream or torch.cuda.current_stream()
     res = {}
     d24 = (24, 24, 24, 48)
-    lat24 = _lattice(d24, kappa, SMEARED_SEED + 1)
+    lat24 = _lattice(d24, kappa, SMEARED_SEED + 1, arith)
     lat24.tune("fp16", 12, 12, stream)
     b = torch.stack([synth.to_host_layout(synth.point_source(d24, s, c)) for s in range(4) for c in range(3)]).cuda()
     x = torch.zeros_like(b)
@@ -67,7 +68,8 @@ def batched(kappa: float, tol: float = 1e-10, stream=None) -> dict:
     del b, x
     torch.cuda.empty_cache()
 
-    lats = [_lattice((8, 8, 8, 8), kappa, SMEARED_SEED + 3), _lattice((16, 16, 16, 32), kappa, SMEARED_SEED), lat24]
+    lats = [_lattice((8, 8, 8, 8), kappa, SMEARED_SEED + 3, arith), _lattice((16, 16, 16, 32), kappa, SMEARED_SEED, arith),
+            lat24]
     bs = [torch.stack([synth.to_host_layout(synth.gaussian_source(l.dims, seed=900 + 10 * i + j)) for j in range(4)]).cuda()
           for i, l in enumerate(lats)]
     xs = [torch.zeros_like(v) for v in bs]
@@ -164,7 +166,8 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
 
 
 def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 128.0, 1024.0, 4096.0),
-            sigma_values=(0.0, 1.0, 16.0, 64.0, 256.0, 1024.0), max_outer: int = 30, source: str = "point") -> dict:
+            sigma_values=(0.0, 1.0, 16.0, 64.0, 256.0, 1024.0), max_outer: int = 30, source: str = "point",
+            arith: int = 32) -> dict:
     """FP16 low-precision matvecs to 1e-10 over the Alg. 2 scale s and the Alg. 3
     residual norm sigma (sigma = 0: no inner rescaling), recalculated gamma, on
     the 16^3 x 32 workload with the paper's unit source (or the Gaussian one)
@@ -176,7 +179,7 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
     report their status and the matvecs spent."""
     stream = stream or torch.cuda.current_stream()
     dims = (16, 16, 16, 32)
-    lat = _lattice(dims, kappa, SMEARED_SEED)
+    lat = _lattice(dims, kappa, SMEARED_SEED, arith)
     if source == "point":
         b = synth.to_host_layout(synth.point_source(dims, 0, 0, 0)).cuda()
     else:
@@ -211,16 +214,17 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
 
 
 
-def clover(wl, csw: float = 1.0, tol: float = 1e-10, stream=None) -> dict:
+def clover(wl, csw: float = 1.0, tol: float = 1e-10, stream=None, arith: int = 32) -> dict:
     """The clover matrix (wd_set_clover) on a workload: FP16-mixed (Alg. 2 + 3)
     against FP64 time to tol, with the Wilson-only solves of the same system
     beside them, and the clover FP16 hop with its C^-1 block (EO operator)."""
     stream = stream or torch.cuda.current_stream()
     lat = wd.Lattice(wl.dims, wl.kappa)
     lat.set_gauge(torch.view_as_real(wl.gauge()).contiguous())
+    lat.set_arith(arith)
     b = synth.to_host_layout(wl.source()).cuda()
     x = torch.zeros_like(b)
-    out = {"csw": csw, "kappa": wl.kappa}
+    out = {"csw": csw, "kappa": wl.kappa, "arith": arith}
     for name, c in (("wilson", 0.0), ("clover", csw)):
         lat.set_clover(c)
         row = {}

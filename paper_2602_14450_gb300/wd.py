@@ -27,7 +27,8 @@ SCHEME = {"fp64": WD_FP64_BICGSTAB, "mixed_fp32": WD_MIXED_FP32, "mixed_fp16_pla
           "mixed_fp16": WD_MIXED_FP16, "mixed_bf16": WD_MIXED_BF16}
 
 # Exported symbols (the declarations of include/wd.h).
-SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_set_clover", "wd_vector_bytes", "wd_pack",
+SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_set_clover", "wd_set_arith",
+           "wd_get_arith", "wd_vector_bytes", "wd_pack",
            "wd_unpack", "wd_apply", "wd_apply_eo_noalloc", "wd_tune", "wd_solve_params_default", "wd_solve",
            "wd_solve_batch",
            "wd_precond_set",
@@ -79,6 +80,8 @@ def lib():
         L.wd_set_gauge.argtypes = [vp, vp, i]
         L.wd_gauge_unitarity.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
         L.wd_set_clover.argtypes = [vp, d]
+        L.wd_set_arith.argtypes = [vp, i]
+        L.wd_get_arith.argtypes = [vp]
         L.wd_vector_bytes.argtypes = [vp, i]
         L.wd_vector_bytes.restype = sz
         L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
@@ -167,6 +170,15 @@ class Lattice:
     def set_clover(self, csw):
         """wd_set_clover: add the clover term with coefficient csw (0 removes it)."""
         self._check(lib().wd_set_clover(self.h, float(csw)), "wd_set_clover")
+
+    def set_arith(self, bits):
+        """wd_set_arith: arithmetic of the FP16-storage hopping term, 32 (FP32) or 16 (FP16, half2)."""
+        self._check(lib().wd_set_arith(self.h, int(bits)), "wd_set_arith")
+
+    @property
+    def arith(self):
+        """wd_get_arith: 32 or 16."""
+        return int(lib().wd_get_arith(self.h))
 
     def unitarity(self):
         a, b = C.c_double(), C.c_double()

@@ -124,7 +124,8 @@ def test_tuned_kernels_match_oracle(prec, recon):
 def test_dslash_error_table():
     """Relative L2 error of H_eo against the oracle for every storage precision
     and link format on the smeared 16^3 x 32 workload (run with -s to print the
-    table): FP16 <= 2e-3, FP32 <= 1e-6, FP64 <= 1e-13."""
+    table): FP16 <= 2e-3, FP32 <= 1e-6, FP64 <= 1e-13; FP16 storage with FP16
+    arithmetic (fp16a) <= 4e-3."""
     dims = (16, 16, 16, 32)
     u = synth.gauge_smeared(dims, seed=20260214)
     psi = synth.gaussian_source(dims, seed=77)
@@ -135,6 +136,68 @@ def test_dslash_error_table():
         err = rel_l2(apply_op(lat, prec, recon, wd.WD_OP_HOP_EO, psi, dims), want)
         rows.append((prec, recon, err))
         assert err <= TOL[prec], (prec, recon, err)
+    lat.set_arith(16)
+    for recon in (18, 12):
+        err = rel_l2(apply_op(lat, "fp16", recon, wd.WD_OP_HOP_EO, psi, dims), want)
+        rows.append(("fp16a", recon, err))
+        assert err <= TOL["fp16a"], ("fp16a", recon, err)
     print("\nH_eo relative L2 error vs the float64 oracle, 16^3 x 32 smeared links:")
     for prec, recon, err in rows:
         print(f"  {prec:5s} {recon:2d}-real  {err:.3e}")
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("recon", [18, 12])
+def test_fp16_arithmetic_matches_oracle(dims, recon):
+    """wd_set_arith(16): the hopping sum in FP16 arithmetic (hop16_kernel)
+    against the oracle, within the FP16-arithmetic bound; its result differs
+    from the FP32-arithmetic kernel's (another kernel ran) by no more than
+    the two bounds together."""
+    u = synth.gauge_random(dims, 0.5, seed=7)
+    psi = synth.gaussian_source(dims, seed=8)
+    kappa = 0.127
+    lat = lattice(u, kappa, dims)
+    for op in (wd.WD_OP_HOP_EO, wd.WD_OP_HOP_OE, wd.WD_OP_EO_A, wd.WD_OP_FULL):
+        lat.set_arith(32)
+        g32 = apply_op(lat, "fp16", recon, op, psi, dims)
+        lat.set_arith(16)
+        assert lat.arith == 16
+        g16 = apply_op(lat, "fp16", recon, op, psi, dims)
+        want = oracle_op(u, psi, op, kappa)
+        err = rel_l2(g16, want)
+        assert err <= TOL["fp16a"], (op, err)
+        if dims != (2, 2, 2, 2):
+            assert not torch.equal(g16, g32)
+        assert rel_l2(g16, g32) <= TOL["fp16a"] + TOL["fp16"]
+        # the other storage precisions ignore the setting
+        assert rel_l2(apply_op(lat, "fp32", recon, op, psi, dims), want) <= TOL["fp32"]
+
+
+def test_fp16_arithmetic_full_size_sampled_sites():
+    """32^3 x 64 in the benchmark's launch configuration with FP16
+    arithmetic: sampled sites of H_eo (boundary corners included) against the
+    oracle."""
+    dims = (32, 32, 32, 64)
+    u = synth.gauge_random(dims, 0.5, seed=20260214)
+    psi = synth.gaussian_source(dims, seed=450)
+    lat = lattice(u, 0.13, dims)
+    lat.set_arith(16)
+    got = apply_op(lat, "fp16", 12, wd.WD_OP_HOP_EO, psi, dims).reshape(-1, 4, 3)
+    par = W.parity(dims).reshape(-1)
+    g = torch.Generator().manual_seed(1)
+    even = torch.nonzero(par == 0).reshape(-1)
+    sample = even[torch.randint(len(even), (4000,), generator=g)]
+    corners = torch.tensor([0, 31, 32 * 31, 32 ** 3 * 63, 32 ** 3 * 64 - 1, 32 ** 3 * 64 - 32])
+    sites = torch.cat([sample, corners[par[corners] == 0]])
+    want = W.hop_at_sites(u, psi, sites, BC)
+    assert rel_l2(got[sites], want) <= TOL["fp16a"]
+
+
+def test_set_arith_rejects_other_widths():
+    lat = wd.Lattice((4, 4, 4, 4), 0.12)
+    assert lat.arith == 32
+    for bits in (0, 8, 64):
+        with pytest.raises(wd.WDError) as e:
+            lat.set_arith(bits)
+        assert e.value.code == wd.WD_ERR_INVALID_ARG
+    assert lat.arith == 32

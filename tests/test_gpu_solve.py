@@ -255,3 +255,35 @@ def test_convergence_history(cfg0):
         if i1 - 1 > i0:
             est, nxt = rows[i1 - 1][2], rows[i1][2]
             assert nxt / 10 <= est <= nxt * 10, (est, nxt)
+
+
+def test_fp16_arithmetic_solves(smeared):
+    """wd_set_arith(16), the paper's FP16 arithmetic in the inner operator:
+    every FP16 scheme still reaches the FP64 tolerance (the refinement
+    absorbs the inner precision) in at most 1.3x the matvecs of FP32
+    arithmetic, also with the paper's flushed subnormals, and the clover
+    operator too."""
+    dims, u, eta, kappa = smeared
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    for scheme, ftz in (("mixed_fp16", 0), ("mixed_fp16", 1), ("mixed_fp16_plain", 0)):
+        counts = {}
+        for bits in (32, 16):
+            lat.set_arith(bits)
+            x = torch.zeros_like(b)
+            p = wd.default_params(scheme)
+            p.ftz = ftz
+            st = lat.solve(b, x, TOL, scheme, params=p)
+            assert st.status == wd.WD_OK and st.true_residual <= TOL, (scheme, bits, st.true_residual)
+            check_solution(dims, u, eta, kappa, from_lex(x, dims))
+            counts[bits] = st.inner_matvecs
+        assert counts[16] <= 1.3 * counts[32] + 8, (scheme, ftz, counts)
+    from oracle import clover as cl
+    lat.set_clover(1.0)
+    lat.set_arith(16)
+    x = torch.zeros_like(b)
+    st = lat.solve(b, x, TOL, "mixed_fp16")
+    assert st.status == wd.WD_OK and st.true_residual <= TOL
+    c = cl.clover_matrix(u, 1.0, kappa)
+    res = S.norm(eta - cl.dirac_sw(u, c, from_lex(x, dims), kappa, BC)) / S.norm(eta)
+    assert res <= TOL
