@@ -121,6 +121,13 @@ typedef struct wd_solve_params {
                              outer scale, (|r| / gamma') |r_outer| / (s^ |eta|)); matvecs =
                              low-precision matvecs so far. NULL = none                       */
     int history_cap;      /* entries `history` holds                                         */
+    int fused_rescale;    /* 1 (default): Alg. 3's rescaling r := (sigma / g) r is applied as r
+                             is formed, with g~^2 = (s,s) - 2 Re(conj(omega) (t,s))
+                             + |omega|^2 (t,t) predicted from the dot products that give
+                             omega (equal to |s - omega t|^2 in exact arithmetic); g itself,
+                             gamma and the stopping test still use the norms of the formed r.
+                             Saves one pass over r and its norms per iteration. 0: a separate
+                             pass after g is known. Alg. 4 always uses the separate pass.   */
 } wd_solve_params;
 
 /* Counters of one solve. */

@@ -5,7 +5,7 @@
 // paper's Fig. 3) and combine threads, blocks and the grid in FP64.
 #pragma once
 
-#include "common.cuh"
+#include "kernels.h"
 
 namespace wd {
 
@@ -78,13 +78,17 @@ __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, 
 }
 
 // x := x + cXr r + cXp p  (x := cXr r + cXp p on the first iteration)
-// r := r - omega t
-// sums: |r|^2, |x|^2, (r*, r) [the last only when WITH_RS]
-template <typename T, bool WITH_RS>
+// r := r - omega t, and with XR_FUSED stored as c (r - omega t), c = sigma / g~
+// the rescaling factor from the predicted norm (ST_OMEGA)
+// sums: XR_PLAIN  |r|^2, |x|^2, (r*, r)
+//       XR_NORMS  |r|^2, |x|^2            (a separate k_scale pass follows)
+//       XR_FUSED  |r|^2 (before scaling), |r_stored|^2, (r*, r_stored)
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
                                             const uint4* t, const uint4* rstar, const uint4* xr_src,
                                             const uint4* xp_src, SolverState* sts, RedCtx rc) {
     typedef typename Unit<T>::C C;
+    constexpr bool WITH_RS = MODE != XR_NORMS;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
     if (guarded(st, GUARD_INNER)) return;
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
     const bool first = st->first;
     const C xr_r = (C)st->cXr[0], xr_i = (C)st->cXr[1], xp_r = (C)st->cXp[0], xp_i = (C)st->cXp[1];
     const C om_r = (C)-st->omega[0], om_i = (C)-st->omega[1];
+    const C gs = MODE == XR_FUSED ? (C)st->gam_tmp : (C)1;
     C s_r2 = 0, s_x2 = 0, s_re = 0, s_im = 0;
     RHS_LOOP(h, n) {
         C rr[24], pp[24], xx[24], tt[24];
@@ -117,11 +122,19 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
         load_spinor<T>(t, n, h, tt);
 #pragma unroll
         for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, tt[2 * i], tt[2 * i + 1]);
-        store_spinor<T>(r, n, h, rr, st->ftz);
 #pragma unroll
-        for (int i = 0; i < 24; ++i) {
-            s_r2 += rr[i] * rr[i];
-            s_x2 += xx[i] * xx[i];
+        for (int i = 0; i < 24; ++i) s_r2 += rr[i] * rr[i];
+        if constexpr (MODE == XR_FUSED) {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) rr[i] *= gs;
+        }
+        store_spinor<T>(r, n, h, rr, st->ftz);
+        if constexpr (MODE == XR_FUSED) {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) s_x2 += rr[i] * rr[i];      // |r_stored|^2
+        } else {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) s_x2 += xx[i] * xx[i];
         }
         if constexpr (WITH_RS) {
             C rs[24];

@@ -368,6 +368,7 @@ struct SolverState {
     double res;                     // |r| / gamma'
     double sigma, sigma_lambda, eps, omega0;
     int recalc, rescale_x, max_matvecs, scale_pass;
+    int fused_scale;                // r is rescaled inside its update (k_xr, XR_FUSED) with the predicted norm
     int iter, matvecs, first, done, status;
     int skip;                       // right-hand side finished: every kernel leaves it alone
     int ftz;                        // flush subnormal values of every low-precision store
@@ -391,7 +392,8 @@ enum Stage {
     ST_END = 5,      // sums: |r_st|^2, (r*, r_st)  -> gamma, beta, convergence
     ST_OUTER = 6,    // sums: |r64|^2               -> outer residual norm
     ST_ACC = 7,      // sums: x                     -> acc += x
-    ST_ACC_SET = 8   // sums: x                     -> acc  = x
+    ST_ACC_SET = 8,  // sums: x                     -> acc  = x
+    ST_RFUSED = 9    // sums: |r|^2, |r_st|^2, (r*, r_st) -> gamma, beta, convergence (rescaling fused)
 };
 
 __device__ __forceinline__ bool finite2(const double* z) { return isfinite(z[0]) && isfinite(z[1]); }
@@ -503,6 +505,14 @@ __device__ inline void run_stage(int stage, const double* s, SolverState* st) {
         }
         st->omega[0] = om[0];
         st->omega[1] = om[1];
+        if (st->fused_scale) {
+            // |s - omega t|^2 = (s,s) - 2 Re(conj(omega) (t,s)) + |omega|^2 (t,t), floored against
+            // cancellation; the factor sigma / g~ rescales r as it is stored
+            double r2 = ss - 2.0 * (om[0] * ts[0] + om[1] * ts[1]) + (om[0] * om[0] + om[1] * om[1]) * tt;
+            r2 = fmax(r2, 1e-12 * ss);
+            st->gam_tmp = st->sigma / sqrt(r2);
+            if (!isfinite(st->gam_tmp)) { stop(st, S_NONFINITE); break; }
+        }
         double c = st->lambda_p / st->gamma_p;
         st->cXr[0] = c * om[0];
         st->cXr[1] = c * om[1];
@@ -527,6 +537,15 @@ __device__ inline void run_stage(int stage, const double* s, SolverState* st) {
         double rn2 = s[0];
         double rs[2] = {s[1], s[2]};
         double gamma = st->sigma > 0.0 ? (st->recalc ? sqrt(rn2) / st->g : st->gam_tmp) : 1.0;
+        end_iteration(st, gamma, rn2, rs);
+        break;
+    }
+    case ST_RFUSED: {
+        double r2 = s[0], rn2 = s[1];
+        double rs[2] = {s[2], s[3]};
+        st->g = sqrt(r2);
+        double gamma = st->recalc ? sqrt(rn2) / st->g : st->gam_tmp;
+        if (r2 == 0.0) gamma = 1.0;   // r = 0 exactly: nothing was scaled, the solve has converged
         end_iteration(st, gamma, rn2, rs);
         break;
     }

@@ -14,6 +14,8 @@ namespace wd {
 
 enum Epi { EPI_H = 0, EPI_Y = 1, EPI_YZ = 2 };
 enum Red { RED_NONE = 0, RED_RSV = 1, RED_TS = 2, RED_NORM = 3 };
+// Rescaling of r in the x/r-update kernel k_xr (Alg. 3): none, norms for a separate k_scale pass, or fused.
+enum XrMode { XR_PLAIN = 0, XR_NORMS = 1, XR_FUSED = 2 };
 
 struct HopParams {
     Geom g;
@@ -57,7 +59,8 @@ template <typename T> struct Ops {
                                const SolverState* st, cudaStream_t s);
     static cudaError_t supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
                                cudaStream_t s);
-    static cudaError_t xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
+    // mode: XrMode
+    static cudaError_t xr(int mode, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
                           const uint4* t, const uint4* rstar, const uint4* xr_src, const uint4* xp_src,
                           SolverState* st, RedCtx rc, cudaStream_t s);
     static cudaError_t scale(int n, int nrhs, long long vs, uint4* r, uint4* x, const uint4* rstar, SolverState* st,

@@ -219,17 +219,20 @@ cudaError_t Ops<T>::supdate(int n, int nrhs, long long vs, uint4* r, const uint4
 }
 
 template <typename T>
-cudaError_t Ops<T>::xr(bool with_rs, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
+cudaError_t Ops<T>::xr(int mode, int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
                        const uint4* t, const uint4* rstar, const uint4* xr_src, const uint4* xp_src,
                        SolverState* st, RedCtx rc, cudaStream_t s) {
-    if (with_rs) {
-        const int nb = reduce_blocks((const void*)k_xr<T, true>, n, VEC_BLOCK, nrhs);
-        k_xr<T, true><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);
-    } else {
-        const int nb = reduce_blocks((const void*)k_xr<T, false>, n, VEC_BLOCK, nrhs);
-        k_xr<T, false><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);
+#define WD_XR_CASE(M)                                                                                        \
+    if (mode == M) {                                                                                         \
+        const int nb = reduce_blocks((const void*)k_xr<T, M>, n, VEC_BLOCK, nrhs);                            \
+        k_xr<T, M><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);   \
+        return cudaGetLastError();                                                                           \
     }
-    return cudaGetLastError();
+    WD_XR_CASE(XR_PLAIN)
+    WD_XR_CASE(XR_NORMS)
+    WD_XR_CASE(XR_FUSED)
+#undef WD_XR_CASE
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

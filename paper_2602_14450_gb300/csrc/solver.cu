@@ -166,7 +166,7 @@ static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, 
 // Enqueue one inner BiCGStab iteration (Alg. 3 / Alg. 4 loop body) of every
 // right-hand side of a system; with a right preconditioner M the operator is
 // A M: v = A (M p), t = A (M s), x += lambda'/gamma' (omega M s + alpha M p).
-static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool scale_pass, bool learned,
+static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, int xr_mode, bool learned,
                                      cudaStream_t s) {
     const int n = S.h->g.Vh, nr = S.nrhs;
     const long long vs = S.vs;
@@ -209,18 +209,20 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, bool sca
         P.rc = red_ctx(h, ST_OMEGA);
         if ((e = Ops<T>::hop(recon, EPI_Y, RED_TS, P, s)) != cudaSuccess) return e;
         // x += lambda'/gamma' (omega s + alpha p) ; r := s - omega t ; |r|, |x|
-        if ((e = Ops<T>::xr(!scale_pass, n, nr, vs, S.xt, S.r, S.p, S.t, S.rs, learned ? S.shat : nullptr,
-                            learned ? S.phat : nullptr, st, red_ctx(h, ST_RNORM), s)) != cudaSuccess)
+        //   (with XR_FUSED r is stored rescaled and the iteration ends here)
+        if ((e = Ops<T>::xr(xr_mode, n, nr, vs, S.xt, S.r, S.p, S.t, S.rs, learned ? S.shat : nullptr,
+                            learned ? S.phat : nullptr, st, red_ctx(h, xr_mode == XR_FUSED ? ST_RFUSED : ST_RNORM),
+                            s)) != cudaSuccess)
             return e;
         // r := (sigma / g) r ; gamma ; [x := lambda x] ; next rho, beta
-        if (scale_pass)
+        if (xr_mode == XR_NORMS)
             if ((e = Ops<T>::scale(n, nr, vs, S.r, S.xt, S.rs, st, red_ctx(h, ST_END), s)) != cudaSuccess) return e;
         return cudaSuccess;
     });
 }
 
 // Capture `iters` iterations of every system plus the activity flag.
-static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_pass, bool learned, int iters,
+static int capture_inner(std::vector<Sys>& sys, int prec, int recon, int xr_mode, bool learned, int iters,
                          cudaGraphExec_t* out) {
     wd_handle* h0 = sys[0].h;
     cudaGraph_t graph = nullptr;
@@ -228,7 +230,7 @@ static int capture_inner(std::vector<Sys>& sys, int prec, int recon, bool scale_
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < iters && e == cudaSuccess; ++i)
         for (auto& S : sys)
-            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, scale_pass, learned, h0->cap);
+            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, xr_mode, learned, h0->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(h0->dflag, 0, sizeof(int), h0->cap);
     for (auto& S : sys) {
         if (e != cudaSuccess) break;
@@ -282,7 +284,10 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         return fail(h0, WD_ERR_INVALID_ARG, "bad solver parameters");
     const int prec = cfg.prec;
     const int recon_lo = cfg.fp64_inner ? 18 : prm.recon;
-    const bool scale_pass = prm.sigma > 0 || prm.rescale_x;
+    // rescaling of r (Alg. 3): none (sigma = 0), fused into the r-update, or a separate pass (also the
+    // pass that rescales x in Alg. 4)
+    const int xr_mode = prm.rescale_x ? XR_NORMS : !(prm.sigma > 0) ? XR_PLAIN : prm.fused_rescale ? XR_FUSED : XR_NORMS;
+    const bool scale_pass = xr_mode == XR_NORMS;
     const int ips = prm.iters_per_sync;
     const int kpi = (scale_pass ? 8 : 7) + (cfg.learned ? 4 : 0);   // kernels per inner iteration
 
@@ -360,16 +365,16 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
     cudaGraphExec_t exec = nullptr;
     bool own_exec = false;
     if (sys.size() == 1) {
-        GraphKey key{prec, recon_lo, (scale_pass ? 1 : 0) | (cfg.learned ? 2 : 0), ips, sys[0].nrhs, h0->gen};
+        GraphKey key{prec, recon_lo, xr_mode | (cfg.learned ? 4 : 0), ips, sys[0].nrhs, h0->gen};
         auto it = h0->graphs.find(key);
         if (it != h0->graphs.end()) {
             exec = it->second;
         } else {
-            if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, cfg.learned, ips, &exec)) != WD_OK) return rc;
+            if ((rc = capture_inner(sys, prec, recon_lo, xr_mode, cfg.learned, ips, &exec)) != WD_OK) return rc;
             h0->graphs[key] = exec;
         }
     } else {
-        if ((rc = capture_inner(sys, prec, recon_lo, scale_pass, cfg.learned, ips, &exec)) != WD_OK) return rc;
+        if ((rc = capture_inner(sys, prec, recon_lo, xr_mode, cfg.learned, ips, &exec)) != WD_OK) return rc;
         own_exec = true;
     }
     long long graph_kernels = 0;
@@ -439,6 +444,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
                     q.recalc = prm.recalc_gamma;
                     q.rescale_x = prm.rescale_x;
                     q.scale_pass = scale_pass ? 1 : 0;
+                    q.fused_scale = xr_mode == XR_FUSED ? 1 : 0;
                     q.ftz = prm.ftz ? 1 : 0;
                     q.hist = hist_on ? dhist : nullptr;
                     q.hist_cap = hist_on ? hist_iters : 0;
@@ -602,6 +608,7 @@ extern "C" int wd_solve_params_default(int scheme, wd_solve_params* p) {
     p->max_inner = 5000;
     p->recon = 12;
     p->iters_per_sync = 8;
+    p->fused_rescale = 1;
     switch (scheme) {
     case WD_FP64_BICGSTAB:
         p->s = 1.0;

@@ -30,15 +30,21 @@ def bytes_per_site(prec: str, recon: int) -> int:
 
 
 def hop_timing(lat, prec: str, recon: int, launches: int, stream=None) -> dict:
-    if prec == "fp16a":
+    """Case "fp16" is FP16 storage with FP32 arithmetic, "fp16a" with FP16
+    arithmetic, whatever the lattice's setting; the setting is restored."""
+    if prec in ("fp16", "fp16a"):
         old = lat.arith
-        lat.set_arith(16)
+        lat.set_arith(16 if prec == "fp16a" else 32)
         try:
-            r = hop_timing(lat, "fp16", recon, launches, stream)
+            r = _hop_timing(lat, "fp16", recon, launches, stream)
         finally:
             lat.set_arith(old)
-        r["case"] = f"fp16a_{recon}"
+        r["case"] = f"{prec}_{recon}"
         return r
+    return _hop_timing(lat, prec, recon, launches, stream)
+
+
+def _hop_timing(lat, prec: str, recon: int, launches: int, stream=None) -> dict:
     from . import wd
     vh = lat.vector_bytes(prec) // (24 * BYTES[prec])
     nb = lat.vector_bytes(prec)

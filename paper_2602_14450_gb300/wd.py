@@ -50,7 +50,7 @@ class SolveParams(C.Structure):
                 ("inner_eps", C.c_double), ("omega0", C.c_double), ("recalc_gamma", C.c_int),
                 ("rescale_x", C.c_int), ("use_shat", C.c_int), ("x_is_guess", C.c_int), ("max_outer", C.c_int),
                 ("max_inner", C.c_int), ("recon", C.c_int), ("ftz", C.c_int), ("iters_per_sync", C.c_int),
-                ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int)]
+                ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int), ("fused_rescale", C.c_int)]
 
 
 class SolveStats(C.Structure):

@@ -287,3 +287,28 @@ def test_fp16_arithmetic_solves(smeared):
     c = cl.clover_matrix(u, 1.0, kappa)
     res = S.norm(eta - cl.dirac_sw(u, c, from_lex(x, dims), kappa, BC)) / S.norm(eta)
     assert res <= TOL
+
+
+def test_fused_rescale_matches_separate_pass(smeared):
+    """wd_solve_params.fused_rescale: Alg. 3's r := (sigma / g) r applied as r is
+    formed (factor from the predicted norm) or in a separate pass once g is
+    known. Both reach the tolerance with matvec counts within 10% of each
+    other, and the fused form launches one kernel fewer per iteration."""
+    dims, u, eta, kappa = smeared
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    out = {}
+    for fused in (1, 0):
+        for recalc in (1, 0):
+            x = torch.zeros_like(b)
+            p = wd.default_params("mixed_fp16")
+            p.fused_rescale, p.recalc_gamma = fused, recalc
+            st = lat.solve(b, x, TOL, "mixed_fp16", params=p)
+            assert st.status == wd.WD_OK and st.true_residual <= TOL, (fused, recalc, st.true_residual)
+            check_solution(dims, u, eta, kappa, from_lex(x, dims))
+            out[fused, recalc] = st
+    for recalc in (1, 0):
+        a, c = out[1, recalc], out[0, recalc]
+        assert abs(a.inner_matvecs - c.inner_matvecs) <= 0.1 * c.inner_matvecs + 4, (a.inner_matvecs, c.inner_matvecs)
+        assert a.kernel_launches / a.inner_iterations < c.kernel_launches / c.inner_iterations
+    assert wd.default_params("mixed_fp16").fused_rescale == 1
