@@ -14,11 +14,14 @@
 // spin components (one packed add per complex number), multiply both by the
 // SU(3) link (the third row of a 12-real link rebuilt in FP16 as well),
 // rebuild and accumulate (one packed FMA per complex number, the boundary
-// phase and the t projector's factor 2 folded into its constant). The 24
-// accumulated reals are rounded to FP16 by those operations themselves; the
-// epilogue (out = a acc + b y + c z and the fused dot products) widens them
-// and runs in FP32 as in every other kernel.
+// phase, the t projector's factor 2 and an exact power-of-two scale of the
+// accumulator folded into its constant). The 24 accumulated reals are rounded
+// to FP16 by those operations themselves; the epilogue (out = a acc + b y + c z
+// and the fused dot products) widens them, undoes the power of two and runs in
+// FP32 as in every other kernel.
 #pragma once
+
+#include <cmath>
 
 #include "hop_impl.cuh"
 
@@ -39,10 +42,23 @@ __device__ __forceinline__ __half2 cmac16(__half2 m, __half2 x, __half2 ix, __ha
     return __hfma2(__high2half2(m), ix, __hfma2(__low2half2(m), x, acc));
 }
 
-// Bits of the half2 constants (1, 1) and (2, 2); XOR 0x80008000 negates both
-// halves, 0x80000000 the high half only, 0x00008000 the low half only.
-constexpr unsigned H2_ONE = 0x3C003C00u;
-constexpr unsigned H2_TWO = 0x40004000u;
+// XOR 0x80008000 negates both halves of a half2 word, 0x80000000 the high half
+// only, 0x00008000 the low half only.
+// Bits of the half2 word (2^k, 2^k), -14 <= k <= 15.
+__host__ __device__ constexpr unsigned h2_pow2(int k) { return ((unsigned)(15 + k) << 10) * 0x10001u; }
+
+// Exponent k of the accumulator scale 2^k: the FP16 sum over the eight
+// directions holds 2^k H in, with 2^k the power of two at or below |a| / 8 (a
+// the epilogue's coefficient of H in), so that it stays in the range of the
+// output a H in with a factor 8 of headroom for partial sums; scaling by a power
+// of two is exact in FP16 above the subnormal range. Clamped to [-14, 0];
+// computed on the host once per launch.
+inline int acc_exponent(double a) {
+    int e = 1;
+    if (a != 0.0) std::frexp(std::fabs(a), &e);   // |a| = m 2^e, 0.5 <= m < 1
+    const int k = e - 1 - 3;
+    return k < -14 ? -14 : (k > 0 ? 0 : k);
+}
 
 // Half spinor h[k * 3 + c] (spin component k, colour c) of the neighbour
 // spinor u (word 3 s + c), projector (1 - gamma_mu) when fwd, else
@@ -159,6 +175,9 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds
     const uint4* vrs = P.rstar ? P.rstar + ro : nullptr;
     const Geom& g = P.g;
     const int Vh = g.Vh;
+    const int ke = P.acc_exp;
+    const unsigned c_one = h2_pow2(ke), c_two = h2_pow2(ke + 1);   // (2^k, 2^k), (2^(k+1), 2^(k+1))
+    const float unscale = __int_as_float((127 - ke) << 23);        // 2^-k
     float part[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) part[k] = 0.f;
@@ -202,12 +221,15 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds
                 __half2 hs[6], chi[6];
                 project16(mu, fwd, cur, hs);
                 link_mul16<R, LF::GROUP_UNITS>(lu, j, hs, chi);
-                const unsigned fb = (mu == 3 ? H2_TWO : H2_ONE) ^ ((((wm >> d) & 1u) && g.bc[mu] < 0) ? 0x80008000u : 0u);
+                const unsigned fb = (mu == 3 ? c_two : c_one) ^ ((((wm >> d) & 1u) && g.bc[mu] < 0) ? 0x80008000u : 0u);
                 reconstruct16(mu, fwd, fb, chi, acc);
             }
         }
 
-        if (EPI == EPI_H && RED == RED_NONE && !MAT && P.a == 1.0) {   // the plain hop: store the FP16 words
+        if (EPI == EPI_H && RED == RED_NONE && !MAT && P.a == 1.0) {   // the plain hop: undo 2^k in FP16 and store
+            const __half2 up = as_h2(h2_pow2(-ke));                      // k = -3 here: (8, 8), exact
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[i] = __hmul2(acc[i], up);
 #pragma unroll
             for (int u = 0; u < SU; ++u) {
                 uint4 w = make_uint4(as_w(acc[4 * u]), as_w(acc[4 * u + 1]), as_w(acc[4 * u + 2]), as_w(acc[4 * u + 3]));
@@ -218,8 +240,8 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds
             float a32[24];
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
-                a32[2 * i] = __low2float(acc[i]);
-                a32[2 * i + 1] = __high2float(acc[i]);
+                a32[2 * i] = __low2float(acc[i]) * unscale;
+                a32[2 * i + 1] = __high2float(acc[i]) * unscale;
             }
             hop_epilogue<__half, EPI, RED, MAT>(P, vout, vy, vz, vrs, h, a32, part, ftz);
         }

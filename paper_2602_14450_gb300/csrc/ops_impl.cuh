@@ -70,14 +70,16 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     if constexpr (std::is_same<T, __half>::value) {
         if (P.arith16) {   // FP16 arithmetic (with or without a site-local block)
             constexpr int blk = Hop16Bounds<R, D, false>::THREADS;
+            HopParams Q = P;
+            Q.acc_exp = acc_exponent(P.a);
             if (P.mat) {
                 const void* km = (const void*)hop16_kernel<R, E, D, true>;
                 const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);
-                hop16_kernel<R, E, D, true><<<nb * P.nrhs, blk, 0, s>>>(P);
+                hop16_kernel<R, E, D, true><<<nb * P.nrhs, blk, 0, s>>>(Q);
             } else {
                 const void* k = (const void*)hop16_kernel<R, E, D, false>;
                 const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
-                hop16_kernel<R, E, D, false><<<nb * P.nrhs, blk, 0, s>>>(P);
+                hop16_kernel<R, E, D, false><<<nb * P.nrhs, blk, 0, s>>>(Q);
             }
             return cudaGetLastError();
         }

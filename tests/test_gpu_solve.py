@@ -312,3 +312,28 @@ def test_fused_rescale_matches_separate_pass(smeared):
         assert abs(a.inner_matvecs - c.inner_matvecs) <= 0.1 * c.inner_matvecs + 4, (a.inner_matvecs, c.inner_matvecs)
         assert a.kernel_launches / a.inner_iterations < c.kernel_launches / c.inner_iterations
     assert wd.default_params("mixed_fp16").fused_rescale == 1
+
+
+@pytest.mark.parametrize("s", [1024.0, 4096.0])
+def test_fp16_arithmetic_large_s_point_source(s):
+    """Alg. 2 with a large s and no inner rescaling (sigma = 0) on the unit
+    source: the first inner input is one element of size s, and the second
+    hop of A sums eight of its neighbours' images before the -kappa^2 factor.
+    The FP16-arithmetic kernel keeps that sum in range (its accumulator is
+    scaled by the power of two below |a| / 8), so the solve converges as with
+    FP32 arithmetic. The lattice is the 16^3 x 32 workload of the parameter
+    tableau, where both settings overflowed with an unscaled FP16 accumulator."""
+    from paper_2602_14450_gb300 import workloads
+    dims = (16, 16, 16, 32)
+    kappa = workloads.KAPPA["16x16x16x32"]
+    u = synth.gauge_smeared(dims, seed=workloads.GAUGE_SEED)
+    eta = synth.point_source(dims, 0, 0, 0)
+    lat = lattice(u, kappa, dims)
+    b = lex_dev(eta)
+    for bits in (32, 16):
+        lat.set_arith(bits)
+        x = torch.zeros_like(b)
+        p = wd.default_params("mixed_fp16")
+        p.s, p.sigma = s, 0.0
+        st = lat.solve(b, x, TOL, "mixed_fp16", params=p, check=False)
+        assert st.status == wd.WD_OK and st.true_residual <= TOL, (bits, st.as_dict())
