@@ -30,6 +30,15 @@ int hop_variant() {
     return v;
 }
 
+int hop16_ahead() {
+    static int v = 0;
+    if (v == 0) {
+        const char* e = std::getenv("WD_HOP16_AHEAD");
+        v = (e && e[0] == '1') ? 1 : 2;
+    }
+    return v;
+}
+
 int num_sms() {
     static int n = 0;
     if (n == 0) {

@@ -25,6 +25,7 @@ __device__ __forceinline__ void cscale_add(C& or_, C& oi, C ar, C ai, C vr, C vi
 template <typename T>
 __global__ void __launch_bounds__(256) k_pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v,
                                                  const uint4* r, const SolverState* sts) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(256) k_pupdate(int n, int nrhs, long long vs, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v,
                                                  const SolverState* sts) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
@@ -87,6 +89,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
                                             const uint4* t, const uint4* rstar, const uint4* xr_src,
                                             const uint4* xp_src, SolverState* sts, RedCtx rc) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     constexpr bool WITH_RS = MODE != XR_NORMS;
     const Slice sl = slice_of(nrhs);
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
 template <typename T>
 __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, uint4* r, uint4* x,
                                                const uint4* rstar, SolverState* sts, RedCtx rc) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;

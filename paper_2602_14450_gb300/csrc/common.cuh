@@ -653,6 +653,16 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc,
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may become resident while its predecessor in the stream is
+// still running. It first waits for that predecessor to complete and its
+// writes to be visible, then lets its own successor start launching. Both
+// instructions do nothing for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Guards: inner-loop kernels return once the inner solve of their right-hand
 // side is done (or the right-hand side is finished); refinement kernels only
 // skip finished right-hand sides.

@@ -149,18 +149,19 @@ __device__ __forceinline__ void reconstruct16(int mu, bool fwd, unsigned fb, con
 }
 
 // Launch shape: one site per thread, 128 threads; the plain hop fits 64
-// registers with 12-real links (8 blocks per SM) and 72 with 18-real links.
-template <int R, int RED, bool MAT> struct Hop16Bounds {
+// registers with 12-real links (8 blocks per SM) and 72 with 18-real links;
+// loading the neighbour spinors two directions ahead (AHEAD = 2) takes 72.
+template <int R, int RED, bool MAT, int AHEAD = 2> struct Hop16Bounds {
     static constexpr int THREADS = 128;
-    static constexpr int MIN_BLOCKS = (RED == RED_NONE && !MAT) ? (R == 12 ? 8 : 7) : 5;
+    static constexpr int MIN_BLOCKS = (RED == RED_NONE && !MAT) ? ((R == 12 && AHEAD == 1) ? 8 : 7) : 5;
 };
 
-// One output site per thread (grid-stride), the neighbour spinor of the next
-// direction and the next link group loaded one step ahead, as in the
-// look-ahead FP32-arithmetic kernel.
-template <int R, int EPI, int RED, bool MAT>
-__global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds<R, RED, MAT>::MIN_BLOCKS)
+// One output site per thread (grid-stride), the neighbour spinors AHEAD
+// directions and the next link group one group ahead of their use.
+template <int R, int EPI, int RED, bool MAT, int AHEAD = 2>
+__global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT, AHEAD>::THREADS, Hop16Bounds<R, RED, MAT, AHEAD>::MIN_BLOCKS)
     hop16_kernel(const HopParams P) {
+    pdl_begin();
     typedef LinkFmt<__half, R> LF;
     constexpr int NS = RedSums<RED>::N;
     constexpr int SU = Spinor<__half>::UNITS;
@@ -189,10 +190,13 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = as_h2(0u);
 
-        uint4 nbu[2][SU];
+        constexpr int NB = AHEAD + 1;   // neighbour slots: the one in use and AHEAD in flight
+        uint4 nbu[NB][SU];
         uint4 lgu[2][LF::GROUP_UNITS];
 #pragma unroll
-        for (int u = 0; u < SU; ++u) nbu[0][u] = __ldg(vin + (size_t)u * Vh + nbr[0]);
+        for (int d = 0; d < AHEAD; ++d)
+#pragma unroll
+            for (int u = 0; u < SU; ++u) nbu[d][u] = __ldg(vin + (size_t)u * Vh + nbr[d]);
 #pragma unroll
         for (int k = 0; k < LF::GROUP_UNITS; ++k) lgu[0][k] = __ldcs(P.links + (size_t)k * Vh + h);
 
@@ -213,10 +217,11 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT>::THREADS, Hop16Bounds
                 const bool fwd = (d & 1) == 0;
                 uint4 cur[SU];
 #pragma unroll
-                for (int u = 0; u < SU; ++u) cur[u] = nbu[d & 1][u];
-                if (d + 1 < 8) {
+                for (int u = 0; u < SU; ++u) cur[u] = nbu[d % NB][u];
+                if (d + AHEAD < 8) {
 #pragma unroll
-                    for (int u = 0; u < SU; ++u) nbu[(d + 1) & 1][u] = __ldg(vin + (size_t)u * Vh + nbr[d + 1]);
+                    for (int u = 0; u < SU; ++u)
+                        nbu[(d + AHEAD) % NB][u] = __ldg(vin + (size_t)u * Vh + nbr[d + AHEAD]);
                 }
                 __half2 hs[6], chi[6];
                 project16(mu, fwd, cur, hs);

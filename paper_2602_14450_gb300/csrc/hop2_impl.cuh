@@ -224,6 +224,7 @@ __device__ __forceinline__ void link_mul2(const uint4 (&ua)[LinkFmt<T, R>::GROUP
 
 template <typename T, int R, int EPI, int RED>
 __global__ void __launch_bounds__(128) hop2_kernel(const HopParams P) {
+    pdl_begin();
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
     constexpr float SC = Wide<T>::SCALE;

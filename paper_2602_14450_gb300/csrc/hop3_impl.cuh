@@ -75,6 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
 
 template <typename T, int R, int EPI, int RED>
 __global__ void __launch_bounds__(128) hop3_kernel(const HopParams P, const StageGeom sg, int* err) {
+    pdl_begin();
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
     constexpr float SC = Wide<T>::SCALE;

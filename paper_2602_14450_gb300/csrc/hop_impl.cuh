@@ -342,6 +342,7 @@ template <typename T, int RED, bool PF, bool MAT = false> struct HopBounds {
 template <typename T, int R, int EPI, int RED, bool PF, bool PAIR = false, bool MAT = false>
 __global__ void __launch_bounds__(HopBounds<T, RED, PF, MAT>::THREADS, HopBounds<T, RED, PF, MAT>::MIN_BLOCKS)
     hop_kernel(const HopParams P) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
     constexpr int NS = RedSums<RED>::N;
@@ -535,6 +536,7 @@ template <typename T, int R> struct RingFmt {
 
 template <typename T, int R, int EPI, int RED>
 __global__ void __launch_bounds__(RingFmt<T, R>::BLOCK, 6) hop_ring_kernel(const HopParams P) {
+    pdl_begin();
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;
     typedef RingFmt<T, R> RF;

@@ -103,6 +103,9 @@ void set_hop_block(int b);
 // with 12-real links, 5 = persistent threads streaming their operands through
 // a per-thread two-slot ring of asynchronous copies in shared memory.
 int hop_variant();
+// Directions ahead that the FP16-arithmetic hop loads its neighbour spinors
+// (environment WD_HOP16_AHEAD = 1 or 2, default 2: 3% faster at 32^3 x 64).
+int hop16_ahead();
 int num_sms();
 
 }  // namespace wd

@@ -1,6 +1,7 @@
 // Definitions of Ops<T>; included by exactly one translation unit per T.
 #pragma once
 
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -14,6 +15,34 @@
 #include "kernels.h"
 
 namespace wd {
+
+// Launch with programmatic stream serialization (programmatic dependent
+// launch): the kernel may be scheduled while its predecessor in the stream
+// finishes, and waits for it in pdl_begin(). Used only for kernels that call
+// pdl_begin() before touching memory. Environment WD_PDL=0 turns it off.
+inline bool pdl_on() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("WD_PDL");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), long grid, int block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_on() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // Resident blocks per SM of a kernel at a block size (cached).
 inline int blocks_per_sm(const void* kernel, int block) {
@@ -69,17 +98,21 @@ template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     if constexpr (std::is_same<T, __half>::value) {
         if (P.arith16) {   // FP16 arithmetic (with or without a site-local block)
-            constexpr int blk = Hop16Bounds<R, D, false>::THREADS;
+            constexpr int blk = Hop16Bounds<R, D, false, 2>::THREADS;
             HopParams Q = P;
             Q.acc_exp = acc_exponent(P.a);
             if (P.mat) {
-                const void* km = (const void*)hop16_kernel<R, E, D, true>;
+                const void* km = (const void*)hop16_kernel<R, E, D, true, 1>;
                 const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);
-                hop16_kernel<R, E, D, true><<<nb * P.nrhs, blk, 0, s>>>(Q);
-            } else {
-                const void* k = (const void*)hop16_kernel<R, E, D, false>;
+                { const cudaError_t le_ = launch_k(hop16_kernel<R, E, D, true, 1>, nb * P.nrhs, blk, 0, s, Q); if (le_ != cudaSuccess) return le_; }
+            } else if (hop16_ahead() == 1) {
+                const void* k = (const void*)hop16_kernel<R, E, D, false, 1>;
                 const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
-                hop16_kernel<R, E, D, false><<<nb * P.nrhs, blk, 0, s>>>(Q);
+                { const cudaError_t le_ = launch_k(hop16_kernel<R, E, D, false, 1>, nb * P.nrhs, blk, 0, s, Q); if (le_ != cudaSuccess) return le_; }
+            } else {
+                const void* k = (const void*)hop16_kernel<R, E, D, false, 2>;
+                const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
+                { const cudaError_t le_ = launch_k(hop16_kernel<R, E, D, false, 2>, nb * P.nrhs, blk, 0, s, Q); if (le_ != cudaSuccess) return le_; }
             }
             return cudaGetLastError();
         }
@@ -88,7 +121,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
         const int blk = 128;
         const void* km = (const void*)hop_kernel<T, R, E, D, true, false, true>;
         const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);
-        hop_kernel<T, R, E, D, true, false, true><<<nb * P.nrhs, blk, 0, s>>>(P);
+        { const cudaError_t le_ = launch_k(hop_kernel<T, R, E, D, true, false, true>, nb * P.nrhs, blk, 0, s, P); if (le_ != cudaSuccess) return le_; }
         return cudaGetLastError();
     }
     constexpr int form = D == RED_NONE ? 0 : 1;
@@ -112,7 +145,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             if (nb > sg.ntiles) nb = sg.ntiles;
             if (nb > MAX_RED_BLOCKS) nb = MAX_RED_BLOCKS;
             if (nb < 1) nb = 1;
-            hop3_kernel<T, R, E, D><<<(int)nb * nr, block, smem, s>>>(P, sg, P.err);
+            { const cudaError_t le_ = launch_k(hop3_kernel<T, R, E, D>, (int)nb * nr, block, smem, s, P, sg, P.err); if (le_ != cudaSuccess) return le_; }
             return cudaGetLastError();
         }
     }
@@ -128,7 +161,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             if (nb > need) nb = need;
             if (D != RED_NONE && nb > MAX_RED_BLOCKS) nb = MAX_RED_BLOCKS;
             if (nb < 1) nb = 1;
-            hop_ring_kernel<T, R, E, D><<<(int)nb * nr, RF::BLOCK, RF::SMEM, s>>>(P);
+            { const cudaError_t le_ = launch_k(hop_ring_kernel<T, R, E, D>, (int)nb * nr, RF::BLOCK, RF::SMEM, s, P); if (le_ != cudaSuccess) return le_; }
             return cudaGetLastError();
         }
     }
@@ -137,7 +170,7 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             const int n = P.g.Vh / 2;
             const void* k2 = (const void*)hop2_kernel<T, R, E, D>;
             const int nb = (D == RED_NONE) ? stream_blocks(n, block) : reduce_blocks(k2, n, block, nr);
-            hop2_kernel<T, R, E, D><<<nb * nr, block, 0, s>>>(P);
+            { const cudaError_t le_ = launch_k(hop2_kernel<T, R, E, D>, nb * nr, block, 0, s, P); if (le_ != cudaSuccess) return le_; }
             return cudaGetLastError();
         }
     }
@@ -145,19 +178,19 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
         if (variant == 6) {   // as 4, with the SU(3) products on FP32x2 column pairs
             const void* k = (const void*)hop_kernel<T, R, E, D, true, true>;
             const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
-            hop_kernel<T, R, E, D, true, true><<<nb * nr, block, 0, s>>>(P);
+            { const cudaError_t le_ = launch_k(hop_kernel<T, R, E, D, true, true>, nb * nr, block, 0, s, P); if (le_ != cudaSuccess) return le_; }
             return cudaGetLastError();
         }
     }
     if (variant == 4) {   // one site per thread, loads one direction ahead
         const void* k = (const void*)hop_kernel<T, R, E, D, true>;
         const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
-        hop_kernel<T, R, E, D, true><<<nb * nr, block, 0, s>>>(P);
+        { const cudaError_t le_ = launch_k(hop_kernel<T, R, E, D, true>, nb * nr, block, 0, s, P); if (le_ != cudaSuccess) return le_; }
         return cudaGetLastError();
     }
     const void* k = (const void*)hop_kernel<T, R, E, D, false>;
     const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, block) : reduce_blocks(k, P.g.Vh, block, nr);
-    hop_kernel<T, R, E, D, false><<<nb * nr, block, 0, s>>>(P);
+    { const cudaError_t le_ = launch_k(hop_kernel<T, R, E, D, false>, nb * nr, block, 0, s, P); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 
@@ -209,14 +242,14 @@ cudaError_t Ops<T>::mat_from64(int n, const uint4* src64, uint4* dst, cudaStream
 template <typename T>
 cudaError_t Ops<T>::pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v, const uint4* r,
                             const SolverState* st, cudaStream_t s) {
-    k_pupdate<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, p, v, r, st);
+    { const cudaError_t le_ = launch_k(k_pupdate<T>, stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, p, v, r, st); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
                             cudaStream_t s) {
-    k_supdate<T><<<stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, r, v, st);
+    { const cudaError_t le_ = launch_k(k_supdate<T>, stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, r, v, st); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 
@@ -227,7 +260,7 @@ cudaError_t Ops<T>::xr(int mode, int n, int nrhs, long long vs, uint4* x, uint4*
 #define WD_XR_CASE(M)                                                                                        \
     if (mode == M) {                                                                                         \
         const int nb = reduce_blocks((const void*)k_xr<T, M>, n, VEC_BLOCK, nrhs);                            \
-        k_xr<T, M><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc);   \
+        { const cudaError_t le_ = launch_k(k_xr<T, M>, nb * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, x, r, p, t, rstar, xr_src, xp_src, st, rc); if (le_ != cudaSuccess) return le_; }   \
         return cudaGetLastError();                                                                           \
     }
     WD_XR_CASE(XR_PLAIN)
@@ -241,7 +274,7 @@ template <typename T>
 cudaError_t Ops<T>::scale(int n, int nrhs, long long vs, uint4* r, uint4* x, const uint4* rstar, SolverState* st,
                           RedCtx rc, cudaStream_t s) {
     const int nb = reduce_blocks((const void*)k_scale<T>, n, VEC_BLOCK, nrhs);
-    k_scale<T><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, r, x, rstar, st, rc);
+    { const cudaError_t le_ = launch_k(k_scale<T>, nb * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, r, x, rstar, st, rc); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 

@@ -607,7 +607,7 @@ extern "C" int wd_solve_params_default(int scheme, wd_solve_params* p) {
     p->max_outer = 100;
     p->max_inner = 5000;
     p->recon = 12;
-    p->iters_per_sync = 8;
+    p->iters_per_sync = 4;
     p->fused_rescale = 1;
     switch (scheme) {
     case WD_FP64_BICGSTAB:
