@@ -152,6 +152,19 @@ def oracle_iteration_seconds(u_cpu, eta, kappa, iters):
     return (time.perf_counter() - t0) / iters, torch.get_num_threads()
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else what the platform module reports."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def stored_oracle_iterations(dims):
     """Float64 iterations the oracle needs on this workload (written by its kappa calibration)."""
     name = "x".join(str(d) for d in dims)
@@ -336,11 +349,20 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_iter = stored_oracle_iterations(wl.dims)
         if n_iter:
+            import torch as _t
             s_it, cores = oracle_iteration_seconds(u.cpu(), eta, wl.kappa, 2)
+            nt = _t.get_num_threads()
+            _t.set_num_threads(1)
+            try:
+                s_one, _ = oracle_iteration_seconds(u.cpu(), eta, wl.kappa, 1)
+            finally:
+                _t.set_num_threads(nt)
             line["cpu_baseline"] = {
-                "value": s_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle",
+                "value": s_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                 "sample": f"2 float64 BiCGStab iterations of the oracle on the full {args.workload} workload "
-                          f"({s_it:.2f} s each), scaled by the {n_iter} iterations it needs to 1e-10"}
+                          f"({s_it:.2f} s each), scaled by the {n_iter} iterations it needs to 1e-10",
+                "one_thread": {"value": s_one * n_iter, "unit": "s", "cores": 1,
+                               "sample": f"1 iteration on one thread ({s_one:.2f} s), scaled likewise"}}
         else:
             line["cpu_baseline"] = None
     if rank == 0:
