@@ -190,7 +190,9 @@ int wd_set_clover(wd_handle* h, double csw);
  * default) widens the stored FP16 values and computes the projection's
  * products, the SU(3) multiplies and the sum over the eight directions in
  * FP32; bits = 16 computes all of them in FP16 (packed half2 operations, one
- * rounding per operation), the arithmetic of the paper's _Float16 build. The
+ * rounding per operation), the arithmetic of the paper's _Float16 build; the
+ * FP16 sum is held scaled by an exact power of two at or below |a| / 8 (a the
+ * coefficient of H in the operation) so that it keeps the output's range. The
  * epilogue of a fused kernel (out = a H in + b y + c z, clover blocks, dot
  * products) stays FP32 and every reduction FP64 in both. Applies to
  * everything the handle does afterwards with WD_FP16 storage: wd_apply,

@@ -17,11 +17,13 @@ def residual(u, eta, kappa, x):
     return S.norm(eta - W.dirac(u, x, kappa, BC)) / S.norm(eta)
 
 
+@pytest.mark.parametrize("arith", [32, 16])
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 4, 8)])
-def test_twelve_spin_colour_point_sources(dims):
+def test_twelve_spin_colour_point_sources(dims, arith):
     u = synth.gauge_smeared(dims, seed=31)
     kappa = 0.125
     lat = lattice(u, kappa, dims)
+    lat.set_arith(arith)
     etas = [synth.point_source(dims, s, c, site=0) for s in range(4) for c in range(3)]
     b = torch.stack([lex_dev(e) for e in etas])
     x = torch.zeros_like(b)
@@ -38,13 +40,15 @@ def test_twelve_spin_colour_point_sources(dims):
     assert S.norm(from_lex(x[5], dims) - ref) / S.norm(ref) < 1e-8
 
 
-def test_uneven_batch_of_lattices():
+@pytest.mark.parametrize("arith", [32, 16])
+def test_uneven_batch_of_lattices(arith):
     specs = [((4, 4, 4, 4), 0.12, 41), ((6, 4, 4, 8), 0.12, 42), ((8, 8, 8, 8), 0.12, 43)]
     lats, bs, xs, etas, us = [], [], [], [], []
     for dims, kappa, seed in specs:
         u = synth.gauge_random(dims, 0.5, seed=seed)
         us.append(u)
         lats.append(lattice(u, kappa, dims))
+        lats[-1].set_arith(arith)
         e = [synth.gaussian_source(dims, seed=100 * seed + j) for j in range(4)]
         etas.append(e)
         bs.append(torch.stack([lex_dev(v) for v in e]))

@@ -76,3 +76,22 @@ def test_clover_batch_and_guards():
     with pytest.raises(wd.WDError) as e:
         lat.solve(b[0], x[0], 1e-10, "mixed_fp16_learned")
     assert e.value.code == wd.WD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("recon", [12, 18])
+def test_clover_operators_fp16_arithmetic(recon):
+    """The clover blocks in the epilogue of the FP16-arithmetic hop
+    (wd_set_arith(16)): the even-odd operator and the full matrix."""
+    dims = (6, 4, 4, 8)
+    u = synth.gauge_random(dims, 0.5, seed=47)
+    psi = synth.gaussian_source(dims, seed=48)
+    kappa = 0.125
+    lat = lattice(u, kappa, dims)
+    lat.set_clover(CSW)
+    lat.set_arith(16)
+    c = cl.clover_matrix(u, CSW, kappa)
+    from oracle import wilson as w
+    want_a = cl.eo_operator_sw(u, torch.linalg.inv(c), w.restrict(psi, 0), kappa, BC)
+    want_d = cl.dirac_sw(u, c, psi, kappa, BC)
+    assert rel_l2(apply_op(lat, "fp16", recon, wd.WD_OP_EO_A, psi, dims), want_a) <= 2 * TOL["fp16a"]
+    assert rel_l2(apply_op(lat, "fp16", recon, wd.WD_OP_FULL, psi, dims), want_d) <= 2 * TOL["fp16a"]
