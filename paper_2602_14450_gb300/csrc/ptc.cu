@@ -1,5 +1,5 @@
 // Learned right preconditioner M: a linear, gauge-equivariant parallel-transport
-// convolution network with channels 1 -> 12 -> 1 (SURVEY a13/a14 form).
+// convolution network with channels 1 -> 12 -> 1, no activation (so M is linear).
 //
 //   layer: out[c](x) = sum_{k=0..8} sum_{c'} W[k, c, c'] (T_k in[c'])(x)
 //   T_0 = 1, T_{1+d} with d = 2 mu: U_mu(x) f(x+mu); d = 2 mu + 1: U_mu(x-mu)^+ f(x-mu)
