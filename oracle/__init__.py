@@ -13,6 +13,10 @@ Plain, slow, float64 restatement of what the paper's method computes:
                  low-precision storage.
 * ``ptc``     -- the learned parallel-transport preconditioner (forward,
                  adjoint and weight gradient) in float64.
+* ``clover``  -- the clover term and the even-odd system with clover blocks.
+* ``arith16`` -- the hopping term evaluated in FP16 arithmetic (every
+                 operation rounded to FP16), the paper's _Float16 build,
+                 emulated in float64.
 
 This package is test infrastructure. Only ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline / reference leg may import it. It shares no

@@ -311,15 +311,22 @@ def solve_wilson(U, eta, kappa: float, bc=(1, 1, 1, -1), tol: float = 1e-12, max
     return w.eo_reconstruct(U, xi_e, eta, kappa, bc), info
 
 
-def low_precision_operator(U, kappa: float, fmt: str, bc=(1, 1, 1, -1), ftz: bool = False):
+def low_precision_operator(U, kappa: float, fmt: str, bc=(1, 1, 1, -1), ftz: bool = False, arith16: bool = False):
     """The even-odd operator with links and every stored vector in ``fmt``.
 
     A_low(p) = store(p - kappa^2 H_eo store(H_oe p)) with rounded links: the
-    odd intermediate is a stored vector like any other.
+    odd intermediate is a stored vector like any other. With ``arith16`` (FP16
+    storage only) both hops are evaluated in FP16 arithmetic
+    (oracle.arith16), the paper's _Float16 build; otherwise exactly.
     """
     from . import wilson as w
     store = make_store(fmt, ftz)
     ul = store(U)
+    if arith16:
+        if fmt != "fp16":
+            raise ValueError("FP16 arithmetic needs FP16 storage")
+        from .arith16 import eo_operator_fp16
+        return (lambda p: eo_operator_fp16(ul, p, kappa, store, bc)), store
 
     def apply(p):
         tmp = store(w.hop_pq(ul, p, 1, bc))
@@ -329,13 +336,15 @@ def low_precision_operator(U, kappa: float, fmt: str, bc=(1, 1, 1, -1), ftz: boo
 
 
 def solve_wilson_mixed(U, eta, kappa: float, bc=(1, 1, 1, -1), fmt: str = "fp16",
-                       outer: OuterParams | None = None, inner: InnerParams | None = None, ftz: bool = False):
-    """Alg. 2 + Alg. 3/4 on the even-odd system, FP64 outer, ``fmt`` inner storage."""
+                       outer: OuterParams | None = None, inner: InnerParams | None = None, ftz: bool = False,
+                       arith16: bool = False):
+    """Alg. 2 + Alg. 3/4 on the even-odd system, FP64 outer, ``fmt`` inner storage
+    (and, with ``arith16``, FP16 arithmetic in the inner operator's hops)."""
     from . import wilson as w
     outer = outer or OuterParams()
     inner = inner or InnerParams()
     b = w.eo_source(U, eta, kappa, bc)
-    a_low, store = low_precision_operator(U, kappa, fmt, bc, ftz)
+    a_low, store = low_precision_operator(U, kappa, fmt, bc, ftz, arith16)
     xi_e, tr = refine(lambda f: w.eo_operator(U, f, kappa, bc), b,
                       lambda y: bicgstab_rescaled(a_low, y, inner, store), store, outer, bref=norm(eta))
     return w.eo_reconstruct(U, xi_e, eta, kappa, bc), tr

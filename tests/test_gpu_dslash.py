@@ -201,3 +201,34 @@ def test_set_arith_rejects_other_widths():
             lat.set_arith(bits)
         assert e.value.code == wd.WD_ERR_INVALID_ARG
     assert lat.arith == 32
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 6, 4, 10)])
+def test_fp16_arithmetic_matches_its_emulation(dims):
+    """hop16_kernel against the oracle's emulation of the same FP16 arithmetic
+    (oracle.arith16, 18-real links so that no link row is rebuilt): the kernel
+    differs from it only where its exactly power-of-two-scaled accumulator
+    reaches the subnormal range, a few units of 2^-24 against values of order
+    one, so the relative L2 distance is bounded by 2e-5, thirty times below
+    the distance of either from float64 (6e-4)."""
+    from oracle import arith16 as A
+    from oracle import solvers as S
+    u64 = synth.gauge_random(dims, 0.5, seed=27)
+    p64 = synth.gaussian_source(dims, seed=28)
+    st = S.make_store("fp16")
+    u, psi = st(u64), st(p64)
+    lat = lattice(u, 0.127, dims)     # FP16 rounding of these links is exact
+    lat.set_arith(16)
+    for op, p in ((wd.WD_OP_HOP_EO, 0), (wd.WD_OP_HOP_OE, 1)):
+        got = apply_op(lat, "fp16", 18, op, psi, dims)
+        want = A.hop_pq_fp16(u, psi, p, BC)
+        err = rel_l2(got, want)
+        same = (got == want).to(torch.float64).mean().item()
+        print(f"\n{dims} op {op}: relative distance {err:.2e}, identical reals {100 * same:.2f}%")
+        assert err <= 2e-5, (op, err)
+        assert rel_l2(got, oracle_op(u64, p64, op, 0.127)) <= TOL["fp16a"]
+    # the even-odd operator: the axpy is FP32 on the GPU and float64 in the
+    # emulation before the FP16 store, which moves a few stored values by one unit
+    got = apply_op(lat, "fp16", 18, wd.WD_OP_EO_A, psi, dims)
+    want = A.eo_operator_fp16(u, W.restrict(psi, 0), 0.127, st, BC)
+    assert rel_l2(got, want) <= 1e-4

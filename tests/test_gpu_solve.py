@@ -97,22 +97,29 @@ def test_restart_from_solution(cfg0):
 
 def test_matvec_counts_match_emulated_oracle(smeared):
     # The oracle runs Alg. 2 + Alg. 3 with FP16 storage emulated on the same
-    # inputs; counts agree within 15% (arithmetic and summation order differ).
+    # inputs (and FP16 arithmetic where the GPU uses it); counts agree within
+    # 15% (summation order and the FP32 parts of the GPU's arithmetic differ).
     dims, u, eta, kappa = smeared
     lat = lattice(u, kappa, dims)
     b = lex_dev(eta)
-    for scheme, fmt, outer, inner in [
-        ("mixed_fp16", "fp16", S.OuterParams(s=128.0), S.InnerParams(sigma=64.0)),
-        ("mixed_fp16_plain", "fp16", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None)),
-        ("mixed_fp32", "fp32", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None)),
+    for scheme, fmt, outer, inner, arith in [
+        ("mixed_fp16", "fp16", S.OuterParams(s=128.0), S.InnerParams(sigma=64.0), 32),
+        ("mixed_fp16_plain", "fp16", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None), 32),
+        ("mixed_fp32", "fp32", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None), 32),
+        # the paper's FP16 arithmetic in the inner operator, against the oracle's emulation of it
+        ("mixed_fp16", "fp16", S.OuterParams(s=128.0), S.InnerParams(sigma=64.0), 16),
+        ("mixed_fp16_plain", "fp16", S.OuterParams(s=1.0, use_shat=False), S.InnerParams(sigma=None), 16),
     ]:
+        lat.set_arith(arith)
         x = torch.zeros_like(b)
         p = wd.default_params(scheme)
         p.recon = 18
         st = lat.solve(b, x, TOL, scheme, params=p)
         assert st.status == wd.WD_OK
-        _, tr = S.solve_wilson_mixed(u, eta, kappa, BC, fmt=fmt, outer=outer, inner=inner)
-        assert abs(st.inner_matvecs - tr.matvecs) <= 0.15 * tr.matvecs + 4, (scheme, st.inner_matvecs, tr.matvecs)
+        _, tr = S.solve_wilson_mixed(u, eta, kappa, BC, fmt=fmt, outer=outer, inner=inner, arith16=arith == 16)
+        assert abs(st.inner_matvecs - tr.matvecs) <= 0.15 * tr.matvecs + 4, (scheme, arith, st.inner_matvecs,
+                                                                              tr.matvecs)
+    lat.set_arith(32)
     # FP64 BiCGStab (Alg. 3 with gamma = 1) against the oracle's float64 run of the same recurrence
     x = torch.zeros_like(b)
     st = lat.solve(b, x, TOL, "fp64")
