@@ -206,11 +206,12 @@ def test_set_arith_rejects_other_widths():
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 6, 4, 10)])
 def test_fp16_arithmetic_matches_its_emulation(dims):
     """hop16_kernel against the oracle's emulation of the same FP16 arithmetic
-    (oracle.arith16, 18-real links so that no link row is rebuilt): the kernel
-    differs from it only where its exactly power-of-two-scaled accumulator
+    (oracle.arith16, 18-real links so that no link row is rebuilt). The two can
+    differ only where the kernel's exactly power-of-two-scaled accumulator
     reaches the subnormal range, a few units of 2^-24 against values of order
-    one, so the relative L2 distance is bounded by 2e-5, thirty times below
-    the distance of either from float64 (6e-4)."""
+    one: at most 0.1% of the reals, and a relative L2 distance below 2e-5,
+    thirty times below the distance of either from float64 (6e-4). On GB300
+    every real of both lattices was identical."""
     from oracle import arith16 as A
     from oracle import solvers as S
     u64 = synth.gauge_random(dims, 0.5, seed=27)
@@ -225,7 +226,7 @@ def test_fp16_arithmetic_matches_its_emulation(dims):
         err = rel_l2(got, want)
         same = (got == want).to(torch.float64).mean().item()
         print(f"\n{dims} op {op}: relative distance {err:.2e}, identical reals {100 * same:.2f}%")
-        assert err <= 2e-5, (op, err)
+        assert err <= 2e-5 and same >= 0.999, (op, err, same)
         assert rel_l2(got, oracle_op(u64, p64, op, 0.127)) <= TOL["fp16a"]
     # the even-odd operator: the axpy is FP32 on the GPU and float64 in the
     # emulation before the FP16 store, which moves a few stored values by one unit
