@@ -262,8 +262,11 @@ typedef struct {
  * thread, FP32x2; not FP64),
  * and for 16-bit storage 3 (tiles staged in shared memory), 6 (FP32x2 column
  * pairs; 64, 128 threads, and 256 for BF16) and, with 12-real links, 5 (per-thread cp.async
- * ring). Not a feature of the paper. Synchronizes `stream`; allocates two
- * scratch vectors of nrhs parity vectors. `out` may be NULL. */
+ * ring). These are the kernels of FP32 arithmetic; with wd_set_arith(16)
+ * the FP16 hops use the FP16-arithmetic kernel, whose shape is fixed (one
+ * site per thread, 128 threads), whatever the tuning. Not a feature of the
+ * paper. Synchronizes `stream`; allocates two scratch vectors of nrhs parity
+ * vectors. `out` may be NULL. */
 int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream, wd_tune_result* out);
 
 /* Fill `p` with the defaults of `scheme` (Table 2 rows; s = 128, sigma = 64
