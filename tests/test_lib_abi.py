@@ -68,3 +68,38 @@ def test_null_handle_is_rejected(L):
     assert L.wd_apply(None, 0, 18, 0, None, None, None) == wd.WD_ERR_INVALID_ARG
     assert L.wd_solve(None, None, None, 1e-10, 0, None, None, None) == wd.WD_ERR_INVALID_ARG
     assert L.wd_vector_bytes(None, 0) == 0
+
+
+def test_arith_entry_points_check_their_arguments(L):
+    assert L.wd_set_arith(None, 16) == wd.WD_ERR_INVALID_ARG
+    assert L.wd_get_arith(None) == 0
+
+
+STRUCTS = {"wd_solve_params": "SolveParams", "wd_solve_stats": "SolveStats", "wd_tune_result": "TuneResult"}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's sizes
+    and field offsets (a C program built against include/wd.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "wd.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in getattr(wd, pyname)._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(wd, pyname)
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
