@@ -70,12 +70,43 @@ def _cscale(c: complex, xr: np.ndarray, xi: np.ndarray):
     return c.real * xr - c.imag * xi, c.real * xi + c.imag * xr
 
 
-def hop_pq_fp16(U: torch.Tensor, psi: torch.Tensor, p: int, bc=(1, 1, 1, -1)) -> torch.Tensor:
+def rebuild_third_row(m_r: np.ndarray, m_i: np.ndarray) -> None:
+    """Row 2 of SU(3) matrices [..., 3, 3] from rows 0 and 1 in FP16
+    arithmetic, in place: row2_b = conj(r0_b1 r1_b2 - r0_b2 r1_b1) with
+    (b1, b2) = (b+1, b+2) mod 3. Each complex product is formed real part of
+    the left factor first, the second product fused into the first:
+    re = Re(a) Re(c) - Im(a) Im(c) - Re(a') Re(c') + Im(a') Im(c'),
+    im = Re(a) Im(c) + Im(a) Re(c) - Re(a') Im(c') - Im(a') Re(c'),
+    a = r0_b1, c = r1_b2, a' = r0_b2, c' = r1_b1, one rounding per term."""
+    for b in range(3):
+        b1, b2 = (b + 1) % 3, (b + 2) % 3
+        ar, ai = m_r[..., 0, b1], m_i[..., 0, b1]
+        cr, ci = m_r[..., 1, b2], m_i[..., 1, b2]
+        a2r, a2i = m_r[..., 0, b2], m_i[..., 0, b2]
+        c2r, c2i = m_r[..., 1, b1], m_i[..., 1, b1]
+        re = r16(ar * cr)
+        re = fma16(ai, -ci, re)
+        re = fma16(-a2r, c2r, re)
+        re = fma16(-a2i, -c2i, re)
+        im = r16(ar * ci)
+        im = fma16(ai, cr, im)
+        im = fma16(-a2r, c2i, im)
+        im = fma16(-a2i, c2r, im)
+        m_r[..., 2, b] = re
+        m_i[..., 2, b] = -im
+
+
+def hop_pq_fp16(U: torch.Tensor, psi: torch.Tensor, p: int, bc=(1, 1, 1, -1), recon: int = 18) -> torch.Tensor:
     """H restricted to outputs on parity p (Eq. 1), in FP16 arithmetic.
 
     U and psi are rounded to FP16 first (they are normally FP16 values
-    already); the result is a full-lattice complex128 field of FP16 values,
-    zero off parity p."""
+    already); with recon = 12 only the first two rows of each link matrix as
+    it is applied (U_mu(x), or U_mu(x - mu)^+ for the backward hop) are
+    kept and the third is rebuilt by rebuild_third_row, which assumes SU(3).
+    The result is a full-lattice complex128 field of FP16 values, zero off
+    parity p."""
+    if recon not in (12, 18):
+        raise ValueError("recon must be 12 or 18")
     dims = dims_of(psi)
     sites, per_mu = _parity_tables(dims, p, bc)
     pm, pp = projectors()
@@ -92,9 +123,12 @@ def hop_pq_fp16(U: torch.Tensor, psi: torch.Tensor, p: int, bc=(1, 1, 1, -1)) ->
         fu = ph_up.real.numpy().reshape(-1, 1)      # +-1 per site
         fd = ph_dn.real.numpy().reshape(-1, 1)
         # forward: U_mu(x); backward: U_mu(x - mu)^+ (conjugate transpose)
-        mf_r, mf_i = uf[mu, site_idx, :, :, 0], uf[mu, site_idx, :, :, 1]
-        mb_r = np.swapaxes(uf[mu, dn, :, :, 0], -1, -2)
+        mf_r, mf_i = uf[mu, site_idx, :, :, 0].copy(), uf[mu, site_idx, :, :, 1].copy()
+        mb_r = np.swapaxes(uf[mu, dn, :, :, 0], -1, -2).copy()
         mb_i = -np.swapaxes(uf[mu, dn, :, :, 1], -1, -2)
+        if recon == 12:
+            rebuild_third_row(mf_r, mf_i)
+            rebuild_third_row(mb_r, mb_i)
         for P, nb, f, m_r, m_i in ((pm[mu].numpy(), up, fu, mf_r, mf_i), (pp[mu].numpy(), dn, fd, mb_r, mb_i)):
             src_r, src_i = pf[nb, :, :, 0] * f[:, :, None], pf[nb, :, :, 1] * f[:, :, None]   # exact phase
             terms, rebuild = split_projector(P)

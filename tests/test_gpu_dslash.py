@@ -203,33 +203,37 @@ def test_set_arith_rejects_other_widths():
     assert lat.arith == 32
 
 
+@pytest.mark.parametrize("recon", [18, 12])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 6, 4, 10)])
-def test_fp16_arithmetic_matches_its_emulation(dims):
+def test_fp16_arithmetic_matches_its_emulation(dims, recon):
     """hop16_kernel against the oracle's emulation of the same FP16 arithmetic
-    (oracle.arith16, 18-real links so that no link row is rebuilt). The two can
-    differ only where the kernel's exactly power-of-two-scaled accumulator
-    reaches the subnormal range, a few units of 2^-24 against values of order
-    one: at most 0.1% of the reals, and a relative L2 distance below 2e-5,
-    thirty times below the distance of either from float64 (6e-4). On GB300
-    every real of both lattices was identical."""
+    (oracle.arith16; with 12-real links the third row is rebuilt in FP16 on
+    both sides). The two can differ only where the kernel's exactly
+    power-of-two-scaled accumulator reaches the subnormal range, a few units
+    of 2^-24 against values of order one: at most 0.1% of the reals, and a
+    relative L2 distance below 2e-5, thirty times below the distance of either
+    from float64 (6e-4). Another rounding order of the rebuilt row would change
+    about 13% of the reals. With 18-real links every real of both lattices was
+    identical on GB300."""
     from oracle import arith16 as A
     from oracle import solvers as S
     u64 = synth.gauge_random(dims, 0.5, seed=27)
     p64 = synth.gaussian_source(dims, seed=28)
     st = S.make_store("fp16")
-    u, psi = st(u64), st(p64)
-    lat = lattice(u, 0.127, dims)     # FP16 rounding of these links is exact
+    psi = st(p64)
+    lat = lattice(u64, 0.127, dims)   # the library rounds the links to FP16 itself
     lat.set_arith(16)
     for op, p in ((wd.WD_OP_HOP_EO, 0), (wd.WD_OP_HOP_OE, 1)):
-        got = apply_op(lat, "fp16", 18, op, psi, dims)
-        want = A.hop_pq_fp16(u, psi, p, BC)
+        got = apply_op(lat, "fp16", recon, op, psi, dims)
+        want = A.hop_pq_fp16(u64, psi, p, BC, recon=recon)
         err = rel_l2(got, want)
         same = (got == want).to(torch.float64).mean().item()
-        print(f"\n{dims} op {op}: relative distance {err:.2e}, identical reals {100 * same:.2f}%")
+        print(f"\n{dims} {recon}-real op {op}: relative distance {err:.2e}, identical reals {100 * same:.2f}%")
         assert err <= 2e-5 and same >= 0.999, (op, err, same)
         assert rel_l2(got, oracle_op(u64, p64, op, 0.127)) <= TOL["fp16a"]
     # the even-odd operator: the axpy is FP32 on the GPU and float64 in the
     # emulation before the FP16 store, which moves a few stored values by one unit
-    got = apply_op(lat, "fp16", 18, wd.WD_OP_EO_A, psi, dims)
-    want = A.eo_operator_fp16(u, W.restrict(psi, 0), 0.127, st, BC)
-    assert rel_l2(got, want) <= 1e-4
+    if recon == 18:
+        got = apply_op(lat, "fp16", 18, wd.WD_OP_EO_A, psi, dims)
+        want = A.eo_operator_fp16(st(u64), W.restrict(psi, 0), 0.127, st, BC)
+        assert rel_l2(got, want) <= 1e-4

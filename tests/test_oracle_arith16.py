@@ -111,3 +111,48 @@ def test_mixed_solve_with_fp16_arithmetic_reaches_fp64_tolerance():
     assert res <= 1e-10
     with pytest.raises(ValueError):
         S.low_precision_operator(u, kappa, "fp32", BC, arith16=True)
+
+
+def su3_signed_permutations(dims, seed):
+    """SU(3) links with entries 0, +-1, +-i: rows 0 and 1 from a signed
+    permutation, row 2 = conj(row 0 x row 1) (exact for such entries)."""
+    u = signed_permutation_links(dims, seed)
+    r0, r1 = u[..., 0, :], u[..., 1, :]
+    u[..., 2, :] = torch.linalg.cross(r0, r1).conj()
+    return u
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_twelve_real_rebuild_exact_for_exact_links(p):
+    """With SU(3) links whose entries are 0, +-1, +-i, the FP16 rebuild of the
+    third row is exact, so the 12-real FP16 hop equals Eq. 1 in float64."""
+    dims = (4, 2, 6, 4)
+    u = su3_signed_permutations(dims, seed=31 + p)
+    assert torch.allclose(torch.linalg.det(u), torch.ones((), dtype=torch.complex128), atol=0)
+    m = torch.view_as_real(u.contiguous()).numpy()
+    mr, mi = m[..., 0].copy(), m[..., 1].copy()
+    A.rebuild_third_row(mr, mi)
+    assert np.array_equal(mr, m[..., 0]) and np.array_equal(mi, m[..., 1])
+    g = torch.Generator().manual_seed(6)
+    shape = (dims[3], dims[2], dims[1], dims[0], 4, 3)
+    psi = (torch.randint(-8, 9, shape, generator=g) + 1j * torch.randint(-8, 9, shape, generator=g)).to(torch.complex128)
+    assert torch.equal(A.hop_pq_fp16(u, psi, p, BC, recon=12), W.hop_pq(u, psi, p, BC))
+
+
+def test_twelve_real_rebuild_on_generic_links():
+    """On FP16-rounded SU(3) links the rebuilt third row is the true one to a
+    few FP16 units (rows 0, 1 carry 2^-12 relative rounding, each rebuilt
+    element sums two products of them in four roundings), and the 12-real hop
+    stays within the FP16-arithmetic bound of float64."""
+    dims = (4, 4, 4, 4)
+    u64 = synth.gauge_random(dims, 0.5, seed=9)
+    m = A.r16(torch.view_as_real(u64.contiguous()).numpy())
+    mr, mi = m[..., 0].copy(), m[..., 1].copy()
+    A.rebuild_third_row(mr, mi)
+    true = torch.view_as_real(u64.contiguous()).numpy()[..., 2, :, :]
+    err = np.abs(np.stack([mr[..., 2, :], mi[..., 2, :]], -1) - true).max()
+    assert err < 8 * 2.0 ** -11
+    psi = synth.gaussian_source(dims, seed=10)
+    assert rel(A.hop_pq_fp16(u64, psi, 0, BC, recon=12), W.hop_pq(u64, psi, 0, BC)) < 4e-3
+    with pytest.raises(ValueError):
+        A.hop_pq_fp16(u64, psi, 0, BC, recon=8)
