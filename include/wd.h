@@ -231,6 +231,13 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
  * - The links of (prec, recon) must already exist: call wd_apply or wd_solve
  *   with them once before (building them allocates); otherwise
  *   WD_ERR_INVALID_ARG.
+ * - With a clover term (wd_set_clover) the result is the clover operator
+ *   in - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe in, as from wd_apply. Its blocks
+ *   C^-1 in precision `prec` must already exist: one wd_apply(WD_OP_EO_A) or
+ *   wd_solve in that precision after wd_set_clover builds them; otherwise
+ *   WD_ERR_INVALID_ARG.
+ * - Uses the kernel configuration wd_tune chose and the FP16 arithmetic of
+ *   wd_set_arith, as wd_apply does, so both give the same bits.
  * - The first call on a device looks up the array's device address; make
  *   that first call outside any stream capture.
  * - All calls on a device share the array: calls that may overlap on the GPU

@@ -64,6 +64,18 @@ extern "C" int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void
         return fail(h, WD_ERR_INVALID_ARG,
                     "wd_apply_eo_noalloc: links of this precision and format are not built yet (building them "
                     "allocates); call wd_apply or wd_solve with them once first");
+    // With a clover term, A = 1 - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe (Eq. 4 with D_ee = C_ee, D_oo = C_oo): the
+    // blocks C^-1 of this precision must exist already, since building them allocates.
+    const uint4* ci_e = nullptr;
+    const uint4* ci_o = nullptr;
+    if (h->have_clover) {
+        ci_e = h->clov[0][prec][0];
+        ci_o = h->clov[0][prec][1];
+        if (!ci_e || !ci_o)
+            return fail(h, WD_ERR_INVALID_ARG,
+                        "wd_apply_eo_noalloc: the clover blocks of this precision are not built yet (building them "
+                        "allocates); call wd_apply(WD_OP_EO_A) or wd_solve with this precision once first");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
@@ -74,10 +86,12 @@ extern "C" int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void
     P.g = h->g;
     P.nrhs = 1;
     P.guard_kind = GUARD_NONE;
-    P.arith16 = (prec == WD_FP16 && h->arith16) ? 1 : 0;
+    apply_tuning(h, prec, recon, P);   // the kernel variant and block of wd_tune, and the FP16 arithmetic
     cudaStream_t s = (cudaStream_t)stream;
     const double k = h->kappa;
-    auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y) {
+    auto hop = [&](int parity, const void* src, void* dst, int epi, double a, double b, const void* y,
+                   const uint4* mat) {
+        P.mat = mat;
         P.parity = parity;
         P.links = parity == 0 ? le : lo;
         P.in = (const uint4*)src;
@@ -90,7 +104,7 @@ extern "C" int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void
             return Ops<T>::hop(recon, epi, RED_NONE, P, s);
         });
     };
-    e = hop(1, in, tmp, EPI_H, 1.0, 0.0, nullptr);                 // tmp = H_oe in (overwrites all of it)
-    if (e == cudaSuccess) e = hop(0, tmp, out, EPI_Y, -k * k, 1.0, in);  // out = in - kappa^2 H_eo tmp
+    e = hop(1, in, tmp, EPI_H, 1.0, 0.0, nullptr, ci_o);                 // tmp = C_oo^-1 H_oe in (all of it)
+    if (e == cudaSuccess) e = hop(0, tmp, out, EPI_Y, -k * k, 1.0, in, ci_e);  // out = in - kappa^2 C_ee^-1 H_eo tmp
     return e == cudaSuccess ? WD_OK : cuda_fail(h, e, "wd_apply_eo_noalloc");
 }

@@ -52,6 +52,55 @@ def test_noalloc_matches_wd_apply_twice(prec, recon, arith):
         assert torch.equal(got, want)
 
 
+def _noalloc(lat, prec, recon, src):
+    out = torch.full_like(src, 0xFF)
+    rc = wd.lib().wd_apply_eo_noalloc(lat.h, wd.PREC[prec], recon, C.c_void_p(src.data_ptr()),
+                                      C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return rc, out
+
+
+@pytest.mark.parametrize("prec,recon,arith", [("fp16", 12, 16), ("fp32", 18, 32), ("fp64", 18, 32)])
+def test_noalloc_with_clover_matches_wd_apply(prec, recon, arith):
+    """With a clover term both entry points give in - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe in (Eq. 4)."""
+    dims = (8, 6, 4, 10)
+    lat = wd.Lattice(dims, 0.125)
+    lat.set_gauge(gauge_host(synth.gauge_random(dims, 0.5, seed=73)))
+    lat.set_arith(arith)
+    src = packed_even(lat, prec, synth.gaussian_source(dims, seed=74))
+    plain = torch.empty_like(src)
+    lat.apply(prec, recon, wd.WD_OP_EO_A, src, plain)        # Wilson A; builds the links
+    lat.set_clover(1.0)
+    rc, _ = _noalloc(lat, prec, recon, src)                 # clover blocks of prec not built yet
+    assert rc == wd.WD_ERR_INVALID_ARG
+    assert b"clover" in wd.lib().wd_last_error(lat.h)
+    ref = torch.empty_like(src)
+    lat.apply(prec, recon, wd.WD_OP_EO_A, src, ref)          # builds the blocks
+    assert not torch.equal(ref, plain)
+    for _ in range(2):
+        rc, out = _noalloc(lat, prec, recon, src)
+        assert rc == wd.WD_OK, wd.lib().wd_last_error(lat.h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("prec,recon", [("fp16", 12), ("bf16", 12), ("fp32", 12)])
+def test_noalloc_after_tune_matches_wd_apply(prec, recon):
+    """After wd_tune both entry points run the tuned kernels and give the same bits."""
+    dims = (8, 8, 8, 16)
+    lat = wd.Lattice(dims, 0.125)
+    lat.set_gauge(gauge_host(synth.gauge_random(dims, 0.5, seed=75)))
+    src = packed_even(lat, prec, synth.gaussian_source(dims, seed=76))
+    ref = torch.empty_like(src)
+    lat.apply(prec, recon, wd.WD_OP_EO_A, src, ref)
+    lat.tune(prec, recon)
+    lat.apply(prec, recon, wd.WD_OP_EO_A, src, ref)
+    for _ in range(2):
+        rc, out = _noalloc(lat, prec, recon, src)
+        assert rc == wd.WD_OK, wd.lib().wd_last_error(lat.h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
 def test_noalloc_refuses_oversized_and_unbuilt():
     dims = (24, 24, 24, 48)                                  # FP64 odd-site vector: 63.7 MB > 16 MiB
     lat = wd.Lattice(dims, 0.12)
