@@ -16,7 +16,10 @@ Plain, slow, float64 restatement of what the paper's method computes:
 * ``clover``  -- the clover term and the even-odd system with clover blocks.
 * ``arith16`` -- the hopping term evaluated in FP16 arithmetic (every
                  operation rounded to FP16), the paper's _Float16 build,
-                 emulated in float64.
+                 emulated in float64 in an order of evaluation read as the
+                 kernel's.
+* ``flops``   -- the hop in Sec. 2's three steps on numbers that count their
+                 own real operations (the 168 flops per hop).
 
 This package is test infrastructure. Only ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline / reference leg may import it. It shares no

@@ -11,6 +11,13 @@ subnormals kept) and a product followed by an addition fused into one
 rounding, as a compiler that contracts a*b + c does. Multiplications by 0,
 +-1, +-2 and +-i are exact and need no rounding.
 
+The paper fixes the arithmetic but not the order of evaluation. The order
+below is a reading chosen to be the CUDA kernel's own, so that the two can be
+compared bit for bit as a regression check of that kernel; it is not
+independent evidence. The parity criterion of the FP16-arithmetic kernel is
+its distance from the float64 Eq. 1 (relative L2 <= 2e-3), which holds for
+any order.
+
 Order of evaluation (the definition emulated here):
   * directions x, y, z, t; for each the forward hop, then the backward one;
   * half spinor: for the two leading nonzero rows k of the projector P,

@@ -8,12 +8,12 @@ from paper_2602_14450_gb300 import synth, wd
 # FP16: inputs and links rounded to 11 significant bits (unit roundoff 2^-11)
 # and FP32 arithmetic; FP32: 2^-24 rounding; BF16: 8 significant bits
 # (2^-8 unit roundoff); FP64: rounding of ~1e3 operations. "fp16a": FP16
-# storage and FP16 arithmetic (wd_set_arith(16)): every output real passes
-# about 20 FP16 roundings (projection, the rebuilt third link row, six packed
-# FMAs per complex product, eight accumulations), each with an error of rms
-# 2^-11/sqrt(3) relative to its operand, which adds up to ~1.3e-3 rms; the
-# bound is three times that.
-TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.6e-2, "fp16a": 4e-3}
+# storage and FP16 arithmetic (wd_set_arith(16)), the benchmark's arithmetic:
+# held to the same 2e-3 as FP16 storage with FP32 arithmetic, the bound the
+# FP16 hopping term is specified to meet against float64. Its roundings
+# (projection, rebuilt third link row, packed FMAs, eight accumulations) stay
+# well inside it (about 7e-4 measured on smeared and on rough links).
+TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.6e-2, "fp16a": 2e-3}
 
 
 def gauge_host(u: torch.Tensor) -> torch.Tensor:

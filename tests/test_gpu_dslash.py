@@ -125,7 +125,7 @@ def test_dslash_error_table():
     """Relative L2 error of H_eo against the oracle for every storage precision
     and link format on the smeared 16^3 x 32 workload (run with -s to print the
     table): FP16 <= 2e-3, FP32 <= 1e-6, FP64 <= 1e-13; FP16 storage with FP16
-    arithmetic (fp16a) <= 4e-3."""
+    arithmetic (fp16a) <= 2e-3."""
     dims = (16, 16, 16, 32)
     u = synth.gauge_smeared(dims, seed=20260214)
     psi = synth.gaussian_source(dims, seed=77)

@@ -42,7 +42,8 @@ def setup():
     return u, lat
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1.5e-2)])
+# FP16 path: BF16 hidden fields (unit roundoff 2^-8) bounded at 1e-2 relative
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1e-2)])
 def test_forward_matches_oracle(setup, prec, tol):
     u, lat = setup
     flat, (w1, w2) = bf16_weights(seed=7)
@@ -128,8 +129,8 @@ def test_collapsed_fp16_path_ragged_tiles(dims):
         lat.precond_apply(prec, packed_even(lat, prec, psi), out)
         outs[prec] = unpacked_even(lat, prec, out, dims)
     assert rel_l2(outs["fp32"], want) <= 2e-6
-    assert rel_l2(outs["fp16"], want) <= 1.5e-2
-    assert rel_l2(outs["fp16"], outs["fp32"]) <= 1.5e-2
+    assert rel_l2(outs["fp16"], want) <= 1e-2
+    assert rel_l2(outs["fp16"], outs["fp32"]) <= 1e-2
 
 
 def test_trained_network_reduces_matvecs():
