@@ -1,6 +1,6 @@
 #!/usr/bin/env python3
 """Benchmark: time to |b - D x| / |b| <= 1e-10 for the Wilson-Dirac system on
-32^3 x 64 with the mixed FP16/FP64 solver (Alg. 2 + Alg. 3), beside the pure
+32^3 x 64 with the mixed FP16/FP64 solver (Alg. 3 + Alg. 4), beside the pure
 FP64 and FP32-mixed forms, and the FP16 Dslash against the HBM roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--arith 16|32]
@@ -139,7 +139,7 @@ def max_over_ranks(v, ws):
 
 def oracle_iteration_seconds(u_cpu, eta, kappa, iters):
     """Seconds per iteration of the oracle's float64 even-odd solve: the
-    Algorithm 3 recurrence with gamma = 1 and the omega_0 prescription, as the
+    Algorithm 4 recurrence with gamma = 1 and the omega_0 prescription, as the
     oracle's kappa calibration counts it (two matrix-vector products each)."""
     import torch
 
@@ -283,7 +283,7 @@ def main():
                 scheme = "mixed_fp16"
                 lat.set_arith(other)
             p = wd.default_params(scheme)
-            if scheme == "mixed_fp16_plain":   # unrescaled FP16 (Alg. 1) crawls: bound its work
+            if scheme == "mixed_fp16_plain":   # unrescaled FP16 (Alg. 2) crawls: bound its work
                 p.max_inner, p.max_outer = 2000, 10
             xs = torch.zeros_like(b)
             q = wd.default_params(scheme)
@@ -332,7 +332,7 @@ def main():
         "config": {"workload": f"wilson_eo_{args.workload}", "lattice": list(wl.dims), "kappa": wl.kappa,
                    "links": "exp(i 0.5 H) + 3 APE steps (alpha 0.5), SU(3)-reprojected; FP16 12-real in the inner solve",
                    "source": f"Gaussian, seed {wl.source_seed}", "tol": TOL,
-                   "scheme": "Alg. 2 + Alg. 3 (s=128, sigma=64, recalculated gamma, eps^2=1e-4)",
+                   "scheme": "Alg. 3 + Alg. 4 (s=128, sigma=64, recalculated gamma, eps^2=1e-4)",
                    "stencil_arith_bits": args.arith,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": bh.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8},

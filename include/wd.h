@@ -6,8 +6,8 @@
  *   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
  *                       + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ],
  * through the even-odd system of Eqs. 4-5 (A = 1 - kappa^2 H_eo H_oe on even
- * sites), with the FP64 iterative refinement of Algorithms 1-2 around the
- * rescaled low-precision BiCGStab of Algorithms 3-4.
+ * sites), with the FP64 iterative refinement of Algorithms 2-3 around the
+ * rescaled low-precision BiCGStab of Algorithms 4-5.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -85,26 +85,26 @@ enum wd_where { WD_HOST = 0, WD_DEVICE = 1 };
 
 /* Solver schemes (Sec. 3 and Table 2). */
 enum wd_scheme {
-    WD_FP64_BICGSTAB = 0,     /* BiCGStab (Alg. 3 with gamma = 1) entirely in FP64       */
-    WD_MIXED_FP32 = 1,        /* Alg. 1 refinement, FP32 inner BiCGStab without rescaling */
-    WD_MIXED_FP16_PLAIN = 2,  /* Alg. 1 refinement, FP16 inner without rescaling          */
-    WD_MIXED_FP16 = 3,        /* Alg. 2 refinement, FP16 inner Alg. 3 / Alg. 4            */
-    WD_MIXED_BF16 = 4,        /* as WD_MIXED_FP16 with BF16 storage (Sec. 6 outlook)      */
+    WD_FP64_BICGSTAB = 0,     /* BiCGStab (Alg. 4 with gamma = 1) entirely in FP64       */
+    WD_MIXED_FP32 = 1,        /* Alg. 2 refinement, FP32 inner BiCGStab without rescaling */
+    WD_MIXED_FP16_PLAIN = 2,  /* Alg. 2 refinement, FP16 inner without rescaling          */
+    WD_MIXED_FP16 = 3,        /* Alg. 3 refinement, FP16 inner Alg. 4 / Alg. 5            */
+    WD_MIXED_BF16 = 4,        /* as WD_MIXED_FP16 with BF16 storage (Sec. 7 outlook)      */
     WD_MIXED_FP16_LEARNED = 5 /* as WD_MIXED_FP16, inner BiCGStab on A M with the learned
                                  right preconditioner M (wd_precond_set first)            */
 };
 
-/* Knobs of Algorithms 1-4. wd_solve_params_default() fills the values a
+/* Knobs of Algorithms 2-5. wd_solve_params_default() fills the values a
  * scheme uses by default. */
 typedef struct wd_solve_params {
-    double s;             /* Alg. 2: norm of the rescaled outer residual y (Alg. 1: 1)      */
-    double sigma;         /* Alg. 3: norm of the inner residual after rescaling; 0 = none  */
-    double sigma_lambda;  /* Alg. 4: norm of the rescaled inner solution                    */
+    double s;             /* Alg. 3: norm of the rescaled outer residual y (Alg. 2: 1)      */
+    double sigma;         /* Alg. 4: norm of the inner residual after rescaling; 0 = none  */
+    double sigma_lambda;  /* Alg. 5: norm of the rescaled inner solution                    */
     double inner_eps;     /* inner stop: |r|/gamma' <= inner_eps * |y~| (eps, not eps^2)    */
     double omega0;        /* omega_0 of the BiCGStab prescription (0.7)                     */
     int recalc_gamma;     /* gamma := |r_stored| / g  instead of sigma / g                   */
-    int rescale_x;        /* Alg. 4 (solution rescaling)                                     */
-    int use_shat;         /* Alg. 2: correct with s^ = |single(y~)| instead of s             */
+    int rescale_x;        /* Alg. 5 (solution rescaling)                                     */
+    int use_shat;         /* Alg. 3: correct with s^ = |single(y~)| instead of s             */
     int x_is_guess;       /* x holds an initial guess (restart from a previous solution)    */
     int max_outer;        /* cap on refinement trips                                         */
     int max_inner;        /* cap on low-precision matrix-vector products per inner solve    */
@@ -121,19 +121,19 @@ typedef struct wd_solve_params {
                              outer scale, (|r| / gamma') |r_outer| / (s^ |eta|)); matvecs =
                              low-precision matvecs so far. NULL = none                       */
     int history_cap;      /* entries `history` holds                                         */
-    int fused_rescale;    /* 1 (default): Alg. 3's rescaling r := (sigma / g) r is applied as r
+    int fused_rescale;    /* 1 (default): Alg. 4's rescaling r := (sigma / g) r is applied as r
                              is formed, with g~^2 = (s,s) - 2 Re(conj(omega) (t,s))
                              + |omega|^2 (t,t) predicted from the dot products that give
                              omega (equal to |s - omega t|^2 in exact arithmetic); g itself,
                              gamma and the stopping test still use the norms of the formed r.
                              Saves one pass over r and its norms per iteration. 0: a separate
-                             pass after g is known. Alg. 4 always uses the separate pass.   */
+                             pass after g is known. Alg. 5 always uses the separate pass.   */
 } wd_solve_params;
 
 /* Counters of one solve. */
 typedef struct wd_solve_stats {
     int status;                /* wd_status of the solve                                 */
-    int outer_iterations;      /* refinement trips (Alg. 1/2 loop bodies)                */
+    int outer_iterations;      /* refinement trips (Alg. 2/3 loop bodies)                */
     int inner_iterations;      /* BiCGStab iterations summed over trips                  */
     int inner_matvecs;         /* low-precision applications of A (2 per iteration)     */
     int outer_matvecs;         /* FP64 applications of A (true residuals)                */
@@ -171,7 +171,7 @@ int wd_gauge_unitarity(wd_handle* h, double* max_unitarity_dev, double* max_det_
  * Q_mu_nu(x) the four plaquettes of the mu-nu plane with a corner at x, each
  * traversed mu-then-nu; the links are periodic. The paper uses the plain
  * Wilson matrix and names the clover matrix as the next one to study
- * (Sec. 6); its even-odd system (Eqs. 4-5) takes the blocks as D_ee, D_oo:
+ * (Sec. 7); its even-odd system (Eqs. 4-5) takes the blocks as D_ee, D_oo:
  *   A = 1 - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe,
  *   b^ = C_ee^-1 (eta_e + kappa H_eo C_oo^-1 eta_o),
  *   xi_o = C_oo^-1 (eta_o + kappa H_oe xi_e).
@@ -280,7 +280,7 @@ int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream, wd_tune_r
  * for WD_MIXED_FP16). */
 int wd_solve_params_default(int scheme, wd_solve_params* p);
 
-/* Solve D_W x = b to |b - D_W x| <= tol |b| (Alg. 2 + Alg. 3/4 around the
+/* Solve D_W x = b to |b - D_W x| <= tol |b| (Alg. 3 + Alg. 4/5 around the
  * even-odd system, Eqs. 4-5). b and x are full-lattice FP64 vectors in the
  * host layout, in host or device memory (detected per pointer; host buffers
  * are copied in and out inside the call). params may be NULL (defaults of
@@ -302,7 +302,7 @@ int wd_solve_batch(int n, wd_handle* const* h, const int* nrhs, const double* co
 
 /* ---- Learned right preconditioner M --------------------------------------
  * A linear, gauge-equivariant parallel-transport network with channels
- * 1 -> 12 -> 1 (not in the paper; its inner solve is the paper's Alg. 3 on
+ * 1 -> 12 -> 1 (not in the paper; its inner solve is the paper's Alg. 4 on
  * A M). One layer maps C_in to C_out quark-field channels:
  *   out[c](x) = sum_{k=0..8} sum_{c'} W[k][c][c'] (T_k in[c'])(x),
  * hop k = 0 is the identity; k = 1 + d for d = 2 mu transports from x + mu with

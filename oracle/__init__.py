@@ -8,8 +8,8 @@ Plain, slow, float64 restatement of what the paper's method computes:
                  matrices and 3x3 links (no spin projection), the even-odd
                  Schur operator and source/reconstruction of Eqs. 4-6, and
                  dense assembly for tiny lattices.
-* ``solvers`` -- textbook BiCGStab, the refinement loops of Algorithms 1-2 and
-                 the rescaled BiCGStab of Algorithms 3-4 with emulated
+* ``solvers`` -- textbook BiCGStab, the refinement loops of Algorithms 2-3 and
+                 the rescaled BiCGStab of Algorithms 4-5 with emulated
                  low-precision storage.
 * ``ptc``     -- the learned parallel-transport preconditioner (forward,
                  adjoint and weight gradient) in float64.

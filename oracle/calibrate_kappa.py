@@ -5,7 +5,7 @@ library calls it.
 
 Rule (applied to each lattice): with APE-smeared links and a Gaussian source
 (seed 450), take the smallest kappa of a grid for which the float64
-comparator solver of Table 2 -- the BiCGStab recurrence of Algorithm 3 with
+comparator solver of Table 2 -- the BiCGStab recurrence of Algorithm 4 with
 gamma = 1 throughout and the omega_0 = 0.7 prescription of Sec. 3, on the
 even-odd system of Eq. 4 -- needs between ``LO`` and ``HI`` matrix-vector
 multiplications (two per iteration; Table 2 and Sec. 6 count a solve's
@@ -88,7 +88,7 @@ def main():
         raise SystemExit("no kappa on the grid gives a count in the window")
     kappa, n = chosen
     with open(out_path, "w") as f:
-        f.write("# Written by oracle/calibrate_kappa.py: oracle float64 even-odd solve, Algorithm 3 recurrence\n")
+        f.write("# Written by oracle/calibrate_kappa.py: oracle float64 even-odd solve, Algorithm 4 recurrence\n")
         f.write(f"# with gamma = 1 and omega_0 = {OMEGA0}, |b_e - A x_e| <= {TOL:g} |eta|.\n")
         f.write(f"# lattice {dims}, APE-smeared links seed {a.seed}, Gaussian source seed {SOURCE_SEED},\n")
         f.write(f"# window {LO}..{HI} matrix-vector multiplications, smallest kappa of the grid {grid} in the window;\n")

@@ -2,7 +2,7 @@
 non-trivial diagonal blocks, float64 -- test infrastructure only.
 
 The paper uses the plain Wilson matrix and names the clover matrix as the
-next one to study (Sec. 6); its even-odd equations (Eqs. 4-5) are written for
+next one to study (Sec. 7); its even-odd equations (Eqs. 4-5) are written for
 general diagonal blocks D_ee, D_oo. With the clover term the Wilson-clover
 matrix is
 

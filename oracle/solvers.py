@@ -2,10 +2,10 @@
 
 * ``bicgstab``          -- textbook BiCGStab (van der Vorst 1992), the plain
                            definition of the solve.
-* ``bicgstab_rescaled`` -- Algorithm 3 (residual rescaling, gamma
+* ``bicgstab_rescaled`` -- Algorithm 4 (residual rescaling, gamma
                            recalculation, omega_0 prescription) and, with
-                           ``rescale_x``, Algorithm 4 (solution rescaling).
-* ``refine``            -- Algorithm 1 (``s = 1``, no s-hat) and Algorithm 2
+                           ``rescale_x``, Algorithm 5 (solution rescaling).
+* ``refine``            -- Algorithm 2 (``s = 1``, no s-hat) and Algorithm 3
                            (rescale the residual to norm s, correct with the
                            norm s-hat of the rounded vector).
 * ``solve_wilson``      -- even-odd solve of Eq. 3 via Eqs. 4-5.
@@ -17,18 +17,18 @@ scalars are float64. Dots are (a, b) = sum conj(a_i) b_i.
 
 Readings of the paper where it is silent or garbled:
 
-* Refinement update (Alg. 1 and 2 print x += t/s and x += t/s-hat): the
+* Refinement update (Alg. 2 and 3 print x += t/s and x += t/s-hat): the
   inner solution approximates A^{-1} y with y = (s/|r|) r, so the update
   that makes one exact inner solve give r = 0 is x += (|r|/s-hat) t; for
-  Alg. 1, s = 1 and s-hat is replaced by 1.
+  Alg. 2, s = 1 and s-hat is replaced by 1.
 * Inner stopping rule ("|r|/gamma' not small enough"): |r|/gamma' <= eps * |b|
   with b the inner right-hand side.
-* Algorithm 4 returns x / lambda' (the stored x is the rescaled solution).
-* Recalculated gamma (Alg. 3/4, "gamma := g/|r|"): the text defines it as the
+* Algorithm 5 returns x / lambda' (the stored x is the rescaled solution).
+* Recalculated gamma (Alg. 4/5, "gamma := g/|r|"): the text defines it as the
   ratio of the residual norms after and before rescaling, i.e. the factor
   that was actually applied, |r_stored| / g; the printed g/|r| is its
   reciprocal and would un-scale p and v. Without rounding it equals sigma/g.
-* sigma = None means gamma = 1 throughout (Alg. 3 without rescaling).
+* sigma = None means gamma = 1 throughout (Alg. 4 without rescaling).
 """
 
 from __future__ import annotations
@@ -142,7 +142,7 @@ def bicgstab(apply_a, b: torch.Tensor, tol: float, maxiter: int = 100000, x0=Non
     return x, info
 
 
-# --- Algorithms 3 and 4 -----------------------------------------------------------
+# --- Algorithms 4 and 5 -----------------------------------------------------------
 
 @dataclass
 class InnerParams:
@@ -150,7 +150,7 @@ class InnerParams:
     eps: float = 1e-2               # inner tolerance (eps^2 = 1e-4, Table 2)
     omega0: float = 0.7             # Sec. 3
     recalc_gamma: bool = True       # gamma := g / |r_stored|
-    rescale_x: bool = False         # Algorithm 4
+    rescale_x: bool = False         # Algorithm 5
     sigma_lambda: float | None = None
     max_matvecs: int = 5000
 
@@ -167,7 +167,7 @@ class InnerTrace:
 
 
 def bicgstab_rescaled(apply_a_low, b: torch.Tensor, prm: InnerParams, store=None, keep_iterates=False):
-    """Algorithm 3 (Alg. 4 with ``prm.rescale_x``) for A x = b, x_0 = 0.
+    """Algorithm 4 (Alg. 5 with ``prm.rescale_x``) for A x = b, x_0 = 0.
 
     ``apply_a_low`` is the low-precision operator (it rounds its own output);
     ``b`` is already in storage precision. Returns (t, trace), t = x / lambda'
@@ -246,12 +246,12 @@ def bicgstab_rescaled(apply_a_low, b: torch.Tensor, prm: InnerParams, store=None
     return x / lam_p, tr
 
 
-# --- Algorithms 1 and 2 ------------------------------------------------------------
+# --- Algorithms 2 and 3 ------------------------------------------------------------
 
 @dataclass
 class OuterParams:
-    s: float = 128.0                # target norm of the rescaled residual (Alg. 2)
-    use_shat: bool = True           # Alg. 2: correct with |single(low_prec(y))|
+    s: float = 128.0                # target norm of the rescaled residual (Alg. 3)
+    use_shat: bool = True           # Alg. 3: correct with |single(low_prec(y))|
     tol: float = 1e-10
     max_outer: int = 100
 
@@ -267,7 +267,7 @@ class RefineTrace:
 
 
 def refine(apply_a, b: torch.Tensor, inner_solve, store, prm: OuterParams, bref: float | None = None):
-    """Algorithm 2 (Alg. 1 with ``s = 1, use_shat = False``); returns (x, trace).
+    """Algorithm 3 (Alg. 2 with ``s = 1, use_shat = False``); returns (x, trace).
 
     Stops when |b - A x| <= tol * bref (bref defaults to |b|). ``inner_solve``
     maps a stored right-hand side to (t, InnerTrace) with t ~ A_low^{-1} y.
@@ -338,7 +338,7 @@ def low_precision_operator(U, kappa: float, fmt: str, bc=(1, 1, 1, -1), ftz: boo
 def solve_wilson_mixed(U, eta, kappa: float, bc=(1, 1, 1, -1), fmt: str = "fp16",
                        outer: OuterParams | None = None, inner: InnerParams | None = None, ftz: bool = False,
                        arith16: bool = False):
-    """Alg. 2 + Alg. 3/4 on the even-odd system, FP64 outer, ``fmt`` inner storage
+    """Alg. 3 + Alg. 4/5 on the even-odd system, FP64 outer, ``fmt`` inner storage
     (and, with ``arith16``, FP16 arithmetic in the inner operator's hops)."""
     from . import wilson as w
     outer = outer or OuterParams()

@@ -1,5 +1,5 @@
-// Fused vector kernels of the rescaled BiCGStab (Alg. 3/4) and of the
-// refinement loop (Alg. 1/2), plus layout conversions. Every kernel streams
+// Fused vector kernels of the rescaled BiCGStab (Alg. 4/5) and of the
+// refinement loop (Alg. 2/3), plus layout conversions. Every kernel streams
 // packed parity vectors unit by unit; reductions keep per-thread partial
 // sums in the arithmetic type (FP32 for low-precision storage, as in the
 // paper's Fig. 3) and combine threads, blocks and the grid in FP64.
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
     grid_reduce<4>(v, rc, sl);
 }
 
-// r := (sigma / g) r, and x := lambda x when rescaling the solution (Alg. 4)
+// r := (sigma / g) r, and x := lambda x when rescaling the solution (Alg. 5)
 // sums: |r|^2, (r*, r)
 template <typename T>
 __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, uint4* r, uint4* x,
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, ui
     grid_reduce<3>(v, rc, sl);
 }
 
-// Rescale the FP64 outer residual and demote it (Alg. 2, first lines):
+// Rescale the FP64 outer residual and demote it (Alg. 3, first lines):
 // y~ = low_prec((s / |r|) r) written to r and r*; sums |single(y~)|^2 and the
 // count of nonzero reals. The product is formed in FP64 and rounded once.
 template <typename T>
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(128) k_chiral_from64(int n, const uint4* src, 
     }
 }
 
-// x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 2 correction; Alg. 1: s^ -> s)
+// x64 += (|r| / s^) * double(t~) / lambda'   (Alg. 3 correction; Alg. 2: s^ -> s)
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(int n, int nrhs, long long vs, long long vs64, uint4* x64,
                                                  const uint4* xt, const SolverState* sts) {

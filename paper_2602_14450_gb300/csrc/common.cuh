@@ -351,7 +351,7 @@ template <typename C> __device__ __forceinline__ cpx<C> mk(C a, C b) { cpx<C> z;
 
 // -------------------------------------------------------- solver scalars ---
 
-// FP64 scalar state of one right-hand side (Alg. 3/4 and the Alg. 1/2 loop).
+// FP64 scalar state of one right-hand side (Alg. 4/5 and the Alg. 2/3 loop).
 // Complex scalars are (re, im) pairs.
 struct SolverState {
     double rho[2], rho_p[2];        // (r*, r) and rho'
@@ -361,7 +361,7 @@ struct SolverState {
     double cXr[2], cXp[2];          // x += cXr r + cXp p     (lambda'/gamma' * (omega, alpha))
     double gamma_p;                 // gamma'
     double lambda_p;                // lambda'
-    double lam;                     // lambda of this iteration (Alg. 4)
+    double lam;                     // lambda of this iteration (Alg. 5)
     double g;                       // |r| before rescaling
     double gam_tmp;                 // sigma / g, the factor applied to r
     double bnorm;                   // |b| of the inner system
@@ -420,7 +420,7 @@ __device__ inline void stop(SolverState* st, int status) {
     if (st->status == S_OK) st->status = status;
 }
 
-// End of a BiCGStab iteration (Alg. 3 last lines): gamma known, r stored.
+// End of a BiCGStab iteration (Alg. 4 last lines): gamma known, r stored.
 // rn2 = |r_stored|^2, rs = (r*, r_stored).
 __device__ inline void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
     double rho_new[2] = {rs[0], rs[1]};
@@ -466,7 +466,7 @@ __device__ inline void run_stage(int stage, const double* s, SolverState* st) {
         st->shat = sqrt(n2);
         st->nonzeros = (long long)s[1];
         st->bnorm = st->use_shat ? st->shat : st->s;
-        // Alg. 3 start: r = r* = y~, p = v = 0, rho' = |r|^2, omega' = alpha' = gamma' = 1
+        // Alg. 4 start: r = r* = y~, p = v = 0, rho' = |r|^2, omega' = alpha' = gamma' = 1
         st->rho[0] = n2; st->rho[1] = 0;
         st->rho_p[0] = n2; st->rho_p[1] = 0;
         st->alpha_p[0] = 1; st->alpha_p[1] = 0;

@@ -14,7 +14,7 @@ namespace wd {
 
 enum Epi { EPI_H = 0, EPI_Y = 1, EPI_YZ = 2 };
 enum Red { RED_NONE = 0, RED_RSV = 1, RED_TS = 2, RED_NORM = 3 };
-// Rescaling of r in the x/r-update kernel k_xr (Alg. 3): none, norms for a separate k_scale pass, or fused.
+// Rescaling of r in the x/r-update kernel k_xr (Alg. 4): none, norms for a separate k_scale pass, or fused.
 enum XrMode { XR_PLAIN = 0, XR_NORMS = 1, XR_FUSED = 2 };
 
 struct HopParams {

@@ -1,5 +1,5 @@
-// Solver driver: FP64 iterative refinement (Alg. 1 / Alg. 2) around the
-// rescaled low-precision BiCGStab (Alg. 3 / Alg. 4) on the even-odd system of
+// Solver driver: FP64 iterative refinement (Alg. 2 / Alg. 3) around the
+// rescaled low-precision BiCGStab (Alg. 4 / Alg. 5) on the even-odd system of
 // Eq. 4, followed by the odd-site reconstruction of Eq. 5, for a batch of
 // systems (lattices), each with one or more right-hand sides.
 //
@@ -163,7 +163,7 @@ static cudaError_t hop64(const Sys& S, int parity, const uint4* in, uint4* out, 
     return Ops<double>::hop(18, epi, red, P, s);
 }
 
-// Enqueue one inner BiCGStab iteration (Alg. 3 / Alg. 4 loop body) of every
+// Enqueue one inner BiCGStab iteration (Alg. 4 / Alg. 5 loop body) of every
 // right-hand side of a system; with a right preconditioner M the operator is
 // A M: v = A (M p), t = A (M s), x += lambda'/gamma' (omega M s + alpha M p).
 static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, int xr_mode, bool learned,
@@ -284,8 +284,8 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
         return fail(h0, WD_ERR_INVALID_ARG, "bad solver parameters");
     const int prec = cfg.prec;
     const int recon_lo = cfg.fp64_inner ? 18 : prm.recon;
-    // rescaling of r (Alg. 3): none (sigma = 0), fused into the r-update, or a separate pass (also the
-    // pass that rescales x in Alg. 4)
+    // rescaling of r (Alg. 4): none (sigma = 0), fused into the r-update, or a separate pass (also the
+    // pass that rescales x in Alg. 5)
     const int xr_mode = prm.rescale_x ? XR_NORMS : !(prm.sigma > 0) ? XR_PLAIN : prm.fused_rescale ? XR_FUSED : XR_NORMS;
     const bool scale_pass = xr_mode == XR_NORMS;
     const int ips = prm.iters_per_sync;
@@ -616,11 +616,11 @@ extern "C" int wd_solve_params_default(int scheme, wd_solve_params* p) {
         p->recon = 18;
         break;
     case WD_MIXED_FP32:
-    case WD_MIXED_FP16_PLAIN:   // Alg. 1: unit-norm input, no s-hat, no inner rescaling
+    case WD_MIXED_FP16_PLAIN:   // Alg. 2: unit-norm input, no s-hat, no inner rescaling
         p->s = 1.0;
         break;
     case WD_MIXED_FP16:
-    case WD_MIXED_BF16:         // Alg. 2 + Alg. 3, Table 2 row s = 128, sigma = 64
+    case WD_MIXED_BF16:         // Alg. 3 + Alg. 4, Table 2 row s = 128, sigma = 64
     case WD_MIXED_FP16_LEARNED:
         p->s = 128.0;
         p->sigma = 64.0;

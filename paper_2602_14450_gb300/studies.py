@@ -133,8 +133,8 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
     (unit real entry at even site 0, spin 0, colour 0) and its stopping rule
     |r|^2 < 1e-26 (|b| = 1, so tol = 1e-13): FP64; FP32 inner (s = 1) with
     eps^2 = 1e-12 and 1e-4; FP16 inner with s = 128, sigma = 64; s = 4096 alone;
-    s = 128, sigma = sigma_lambda = 256 with solution rescaling (Alg. 4); and
-    unrescaled FP16 (Alg. 1), the paper's unimproved case -- the last and the
+    s = 128, sigma = sigma_lambda = 256 with solution rescaling (Alg. 5); and
+    unrescaled FP16 (Alg. 2), the paper's unimproved case -- the last and the
     first FP16 row also with subnormals flushed to zero on every store, the
     regime of the paper's build."""
     stream = stream or torch.cuda.current_stream()
@@ -147,10 +147,10 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
         "fp16_s128_sigma64": ("mixed_fp16", {}),
         "fp16_s4096": ("mixed_fp16", {"s": 4096.0, "sigma": 0.0}),
         "fp16_s128_sigma256_lambda256": ("mixed_fp16", {"sigma": 256.0, "sigma_lambda": 256.0, "rescale_x": 1}),
-        "fp16_unrescaled_alg1": ("mixed_fp16_plain", {}),
+        "fp16_unrescaled_alg2": ("mixed_fp16_plain", {}),
         # the paper's build flushes subnormals (-Kfz): the same two FP16 forms with every store flushed
         "fp16_s128_sigma64_ftz": ("mixed_fp16", {"ftz": 1}),
-        "fp16_unrescaled_alg1_ftz": ("mixed_fp16_plain", {"ftz": 1}),
+        "fp16_unrescaled_alg2_ftz": ("mixed_fp16_plain", {"ftz": 1}),
     }
     out = {"source": "b = (1, 0, ..., 0): even site 0, spin 0, colour 0", "tol": tol}
     for name, (scheme, kw) in rows.items():
@@ -168,12 +168,12 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
 def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 128.0, 1024.0, 4096.0),
             sigma_values=(0.0, 1.0, 16.0, 64.0, 256.0, 1024.0), max_outer: int = 30, source: str = "point",
             arith: int = 32) -> dict:
-    """FP16 low-precision matvecs to 1e-10 over the Alg. 2 scale s and the Alg. 3
+    """FP16 low-precision matvecs to 1e-10 over the Alg. 3 scale s and the Alg. 4
     residual norm sigma (sigma = 0: no inner rescaling), recalculated gamma, on
     the 16^3 x 32 workload with the paper's unit source (or the Gaussian one)
-    -- the counts Sec. 5 plots in its parameter study --
+    -- the counts Sec. 6 plots in its parameter study --
     plus the four corners of recalculated gamma on/off and solution rescaling
-    (Alg. 4, sigma_lambda = sigma) on/off at s = 128, sigma = 64, and Alg. 1
+    (Alg. 5, sigma_lambda = sigma) on/off at s = 128, sigma = 64, and Alg. 2
     with unrescaled FP16 (the paper's unimproved case). Inner solves stop at 2000
     matvecs and the refinement at max_outer trips; runs that stop at the caps
     report their status and the matvecs spent."""
@@ -206,8 +206,8 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
         for lam in (0, 1):
             corners[f"recalc_gamma={recalc},rescale_x={lam}"] = run("mixed_fp16", recalc_gamma=recalc, rescale_x=lam)
     out = {"lattice": list(dims), "kappa": kappa, "source": source, "grid": grid, "corners": corners,
-           "fp16_unrescaled_alg1": run("mixed_fp16_plain"),
-           "fp32_alg1_eps2_1e-4": run("mixed_fp32"),
+           "fp16_unrescaled_alg2": run("mixed_fp16_plain"),
+           "fp32_alg2_eps2_1e-4": run("mixed_fp32"),
            "fp64": run("fp64")}
     lat.close()
     return out
@@ -215,7 +215,7 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
 
 
 def clover(wl, csw: float = 1.0, tol: float = 1e-10, stream=None, arith: int = 32) -> dict:
-    """The clover matrix (wd_set_clover) on a workload: FP16-mixed (Alg. 2 + 3)
+    """The clover matrix (wd_set_clover) on a workload: FP16-mixed (Alg. 3 + 4)
     against FP64 time to tol, with the Wilson-only solves of the same system
     beside them, and the clover FP16 hop with its C^-1 block (EO operator)."""
     stream = stream or torch.cuda.current_stream()

@@ -1,4 +1,4 @@
-"""Synthetic workloads standing in for the paper's lattice (Sec. 5).
+"""Synthetic workloads standing in for the paper's lattice (Sec. 6).
 
 The paper solves on 32^3 x 64 with kappa = 0.13, a stout-smeared test
 configuration tiled from 4^3 x 8 and the even-odd unit source; that

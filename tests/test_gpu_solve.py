@@ -55,7 +55,7 @@ def test_schemes_reach_fp64_residual(cfg0, scheme):
     check_solution(dims, u, eta, kappa, from_lex(x, dims), ref)
 
 
-def test_alg4_solution_rescaling(cfg0):
+def test_alg5_solution_rescaling(cfg0):
     dims, u, eta, kappa, ref = cfg0
     lat = lattice(u, kappa, dims)
     p = wd.default_params("mixed_fp16")
@@ -96,7 +96,7 @@ def test_restart_from_solution(cfg0):
 
 
 def test_matvec_counts_match_emulated_oracle(smeared):
-    # The oracle runs Alg. 2 + Alg. 3 with FP16 storage emulated on the same
+    # The oracle runs Alg. 3 + Alg. 4 with FP16 storage emulated on the same
     # inputs (and FP16 arithmetic where the GPU uses it); counts agree within
     # 15% (summation order and the FP32 parts of the GPU's arithmetic differ).
     dims, u, eta, kappa = smeared
@@ -120,7 +120,7 @@ def test_matvec_counts_match_emulated_oracle(smeared):
         assert abs(st.inner_matvecs - tr.matvecs) <= 0.15 * tr.matvecs + 4, (scheme, arith, st.inner_matvecs,
                                                                               tr.matvecs)
     lat.set_arith(32)
-    # FP64 BiCGStab (Alg. 3 with gamma = 1) against the oracle's float64 run of the same recurrence
+    # FP64 BiCGStab (Alg. 4 with gamma = 1) against the oracle's float64 run of the same recurrence
     x = torch.zeros_like(b)
     st = lat.solve(b, x, TOL, "fp64")
     bhat = W.eo_source(u, eta, kappa, BC)
@@ -131,7 +131,7 @@ def test_matvec_counts_match_emulated_oracle(smeared):
 
 
 def test_first_inner_input_single_nonzero():
-    # Sec. 5: b = (1, 0, ..., 0) on the even-odd system: one nonzero real in
+    # Sec. 6: b = (1, 0, ..., 0) on the even-odd system: one nonzero real in
     # the first low-precision input.
     dims = (8, 8, 8, 8)
     u = synth.gauge_smeared(dims, seed=1)
@@ -173,7 +173,7 @@ def test_iteration_caps_report_not_converged(cfg0):
 
 @pytest.mark.parametrize("scale", [1e-150, 1e150])
 def test_extreme_source_norms(cfg0, scale):
-    # The outer rescaling (Alg. 2) keeps the FP16 inner input at norm s for
+    # The outer rescaling (Alg. 3) keeps the FP16 inner input at norm s for
     # any |b|; a first rho' = |r|^2 keeps beta = 1 (Sec. 3).
     dims, u, eta, kappa, ref = cfg0
     lat = lattice(u, kappa, dims)
@@ -185,12 +185,12 @@ def test_extreme_source_norms(cfg0, scale):
 
 
 def test_flush_to_zero_regime_of_the_paper():
-    """Sec. 5 (Figs. 5 and 7): with the unit source b = (1, 0, ..., 0) and FP16
+    """Sec. 6 (Figs. 5 and 7): with the unit source b = (1, 0, ..., 0) and FP16
     subnormals flushed to zero on every store (the paper's -Kfz build), the
-    unrescaled inner solve of Alg. 1 loses vector elements to underflow and
+    unrescaled inner solve of Alg. 2 loses vector elements to underflow and
     needs several times the matvecs of the unflushed run, while the rescaled
-    Alg. 2 + Alg. 3 is unaffected. The oracle's emulation of the same solves
-    on this lattice gives 3804 vs 476 (Alg. 1) and 434 vs 470 (Alg. 2 + 3)."""
+    Alg. 3 + Alg. 4 is unaffected. The oracle's emulation of the same solves
+    on this lattice gives 3804 vs 476 (Alg. 2) and 434 vs 470 (Alg. 3 + 4)."""
     dims = (8, 8, 8, 16)
     kappa = 0.1265
     u = synth.gauge_smeared(dims, seed=5)
@@ -297,7 +297,7 @@ def test_fp16_arithmetic_solves(smeared):
 
 
 def test_fused_rescale_matches_separate_pass(smeared):
-    """wd_solve_params.fused_rescale: Alg. 3's r := (sigma / g) r applied as r is
+    """wd_solve_params.fused_rescale: Alg. 4's r := (sigma / g) r applied as r is
     formed (factor from the predicted norm) or in a separate pass once g is
     known. Both reach the tolerance with matvec counts within 10% of each
     other, and the fused form launches one kernel fewer per iteration."""
@@ -323,7 +323,7 @@ def test_fused_rescale_matches_separate_pass(smeared):
 
 @pytest.mark.parametrize("s", [1024.0, 4096.0])
 def test_fp16_arithmetic_large_s_point_source(s):
-    """Alg. 2 with a large s and no inner rescaling (sigma = 0) on the unit
+    """Alg. 3 with a large s and no inner rescaling (sigma = 0) on the unit
     source: the first inner input is one element of size s, and the second
     hop of A sums eight of its neighbours' images before the -kappa^2 factor.
     The FP16-arithmetic kernel keeps that sum in range (its accumulator is

@@ -99,7 +99,7 @@ def test_error_between_exact_arithmetic_and_the_kernel_bound():
 
 
 def test_mixed_solve_with_fp16_arithmetic_reaches_fp64_tolerance():
-    """Alg. 2 + Alg. 3 with the inner operator in FP16 arithmetic: the FP64
+    """Alg. 3 + Alg. 4 with the inner operator in FP16 arithmetic: the FP64
     refinement still reaches 1e-10 in the full system."""
     dims = (4, 4, 4, 4)
     u = synth.gauge_random(dims, 0.5, seed=21)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's solvers (Sec. 3, Algorithms 1-4).
+"""Pins of the oracle's solvers (Sec. 3, Algorithms 2-5).
 
 Pinned by: a dense LU solve; exact invariances of the rescaled recurrences in
 float64 (rescaling by any sigma, solution rescaling, gamma = 1 and omega_0 = 0
@@ -57,7 +57,7 @@ def test_gamma_one_omega0_zero_is_textbook(system):
 
 @pytest.mark.parametrize("sigma,recalc", [(64.0, True), (64.0, False), (1e4, True), (1e-3, True)])
 def test_residual_rescaling_is_exact_in_fp64(system, sigma, recalc):
-    # Alg. 3 with any sigma computes the same iterates as gamma = 1 in exact
+    # Alg. 4 with any sigma computes the same iterates as gamma = 1 in exact
     # arithmetic; in float64 they agree to rounding.
     _, _, b, a = system
     base = S.InnerParams(sigma=None, eps=0.0, max_matvecs=24)
@@ -71,7 +71,7 @@ def test_residual_rescaling_is_exact_in_fp64(system, sigma, recalc):
         assert abs(r1 - r0) <= 1e-11 * r0
 
 
-def test_solution_rescaling_alg4_equals_alg3_in_fp64(system):
+def test_solution_rescaling_alg5_equals_alg4_in_fp64(system):
     _, _, b, a = system
     p3 = S.InnerParams(sigma=256.0, eps=0.0, max_matvecs=24)
     p4 = S.InnerParams(sigma=256.0, rescale_x=True, sigma_lambda=256.0, eps=0.0, max_matvecs=24)
@@ -90,7 +90,7 @@ def test_first_beta_is_one(system, scale):
 
 
 def test_refinement_one_step_exact_with_exact_inner(system):
-    # Reading of Alg. 2's correction: x += (|r| / s-hat) t makes one exact
+    # Reading of Alg. 3's correction: x += (|r| / s-hat) t makes one exact
     # inner solve give r = 0. The literal x += t / s-hat does not (|r| != 1).
     _, _, b, a = system
     b = 1e3 * b
@@ -107,7 +107,7 @@ def test_refinement_one_step_exact_with_exact_inner(system):
 
 
 def test_first_inner_input_has_one_nonzero():
-    # Sec. 5: for b = (1, 0, ..., 0) the first inner input has 1 nonzero
+    # Sec. 6: for b = (1, 0, ..., 0) the first inner input has 1 nonzero
     # among the 25,165,824 reals of an even-odd vector at 32^3 x 64.
     nums = read_numbers()
     assert (32 ** 3 * 64 // 2) * 24 == nums["first_inner_input_elements"]
@@ -141,7 +141,7 @@ def test_mixed_solver_reaches_fp64_residual(system, fmt, outer, inner):
 
 
 def test_storage_rounding_formats():
-    # FP16: 11-bit significand, max 65504, min normal 2^-14 ~ 6.10e-5 (Sec. 4, Table 1).
+    # FP16: 11-bit significand, max 65504, min normal 2^-14 ~ 6.10e-5 (Sec. 5, Table 1).
     st = S.make_store("fp16")
     v = torch.tensor([1 + 2 ** -11, 1 + 3 * 2 ** -11, 65504.0, 65520.0, 2 ** -24, 2 ** -25], dtype=torch.float64)
     got = torch.view_as_real(st(torch.complex(v, torch.zeros_like(v))))[:, 0]
@@ -152,7 +152,7 @@ def test_storage_rounding_formats():
 
 
 def test_inner_breakdown_stops_without_raising():
-    """Algorithm 3 breaks down when (r*, v) = 0 (here A = 0): the oracle stops
+    """Algorithm 4 breaks down when (r*, v) = 0 (here A = 0): the oracle stops
     the inner solve with x = 0 and flags it, as the device recurrence does
     (status breakdown, the refinement continues), instead of dividing by zero."""
     b = torch.randn(40, dtype=torch.complex128, generator=torch.Generator().manual_seed(3))
@@ -163,9 +163,9 @@ def test_inner_breakdown_stops_without_raising():
 
 
 def test_fp16_flush_to_zero_slows_unrescaled_inner_solve():
-    """Sec. 5: with the paper's unit source and FP16 subnormals flushed to zero
-    (its -Kfz build), the unrescaled inner solve of Alg. 1 loses vector
-    elements to underflow and needs far more matvecs, while Alg. 2 + Alg. 3
+    """Sec. 6: with the paper's unit source and FP16 subnormals flushed to zero
+    (its -Kfz build), the unrescaled inner solve of Alg. 2 loses vector
+    elements to underflow and needs far more matvecs, while Alg. 3 + Alg. 4
     (s = 128, sigma = 64) keeps its vectors in range and is unaffected. Without
     the flush the two cost the same. (On 8^3 x 16 the gap is 3804 vs 434.)"""
     from oracle import wilson as W
@@ -176,15 +176,15 @@ def test_fp16_flush_to_zero_slows_unrescaled_inner_solve():
     runs = {}
     for ftz in (False, True):
         for name, outer, inner in [
-            ("alg1", S.OuterParams(s=1.0, use_shat=False, tol=1e-13, max_outer=25),
+            ("alg2", S.OuterParams(s=1.0, use_shat=False, tol=1e-13, max_outer=25),
              S.InnerParams(sigma=None, max_matvecs=600)),
-            ("alg23", S.OuterParams(s=128.0, use_shat=True, tol=1e-13, max_outer=25),
+            ("alg34", S.OuterParams(s=128.0, use_shat=True, tol=1e-13, max_outer=25),
              S.InnerParams(sigma=64.0, max_matvecs=600)),
         ]:
             x, tr = S.solve_wilson_mixed(u, eta, 0.124, fmt="fp16", outer=outer, inner=inner, ftz=ftz)
             assert tr.converged and S.norm(eta - W.dirac(u, x, 0.124)) / S.norm(eta) <= 1e-13
             runs[name, ftz] = tr
     n = 2 * dims[0] * dims[1] * dims[2] * dims[3] // 2 * 12       # reals of an even-site vector
-    assert runs["alg1", False].nonzeros[1] == n and runs["alg1", True].nonzeros[1] < n
-    assert runs["alg1", True].matvecs >= 1.4 * runs["alg1", False].matvecs
-    assert abs(runs["alg23", True].matvecs - runs["alg23", False].matvecs) <= 0.1 * runs["alg23", False].matvecs
+    assert runs["alg2", False].nonzeros[1] == n and runs["alg2", True].nonzeros[1] < n
+    assert runs["alg2", True].matvecs >= 1.4 * runs["alg2", False].matvecs
+    assert abs(runs["alg34", True].matvecs - runs["alg34", False].matvecs) <= 0.1 * runs["alg34", False].matvecs
