@@ -244,6 +244,76 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
  *   (different streams without ordering) race and give wrong results. */
 int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void* in, void* out, void* stream);
 
+/* ---- Domain decomposition ------------------------------------------------
+ * The global lattice is split into a grid of sub-lattices, one per process
+ * (the paper runs 64 MPI processes, Sec. 6, and sums every global reduction
+ * in FP64 across them, Sec. 5, Fig. 3). Each process creates a handle with
+ * its LOCAL extents (every one even, so a site's parity is the same in local
+ * and global coordinates; the global extent in mu is grid[mu] times the
+ * local one), loads its local links (wd_set_gauge, local lexicographic
+ * order) and calls wd_dd_set_partition. The hopping term H_pq of Eq. 1 on
+ * the sub-lattice is then
+ *   H = (interior hops, wd_dd_hop_interior) + (face hops, wd_dd_hop_faces),
+ * the face hops built from half spinors the neighbours packed (wd_dd_pack)
+ * and the caller moved (MPI, NCCL, or copies). Per direction mu with
+ * grid[mu] > 1 there are 8 face buffers send[d] / recv[d], d = 2 mu + side:
+ *   side 0: the lower face x_mu = 0 of `in`, (1 - gamma_mu) in, two spin rows;
+ *           send[2 mu] goes to the neighbour at coords[mu] - 1, whose
+ *           recv[2 mu] it becomes;
+ *   side 1: the upper face x_mu = L_mu - 1 of `in`, U_mu(x)^+ (1 + gamma_mu) in;
+ *           send[2 mu + 1] goes to the neighbour at coords[mu] + 1, whose
+ *           recv[2 mu + 1] it becomes;
+ * (coordinates modulo grid[mu]; with grid[mu] = 2 both go to the same
+ * neighbour and must stay apart). A face buffer holds wd_dd_face_bytes(mu)
+ * bytes: 12 reals of the storage precision per face site, real e of face
+ * site f at element e * F + f, F = V_local / 2 / L_mu, f = the
+ * lexicographic index of the three other local coordinates (lowest
+ * direction fastest) halved. Buffers of directions that are not split are
+ * ignored (may be NULL). The boundary phase bc[mu] of a hop that wraps
+ * around the global lattice is applied by the packing process. Arithmetic
+ * as in enum wd_prec. Not available with a clover term or the learned
+ * preconditioner; on a split handle wd_apply, wd_solve, wd_solve_batch and
+ * wd_precond_* return WD_ERR_INVALID_ARG. */
+
+/* Declare this handle the sub-lattice at `coords` of a process grid `grid`
+ * (grid[mu] >= 1, 0 <= coords[mu] < grid[mu]); the handle's boundary phases
+ * bc are those of the global lattice. All grid[mu] = 1 undoes the split.
+ * Packed links built before are rebuilt on next use. */
+int wd_dd_set_partition(wd_handle* h, const int grid[4], const int coords[4]);
+
+/* Bytes of one face buffer of direction mu in precision prec (0 on bad input). */
+size_t wd_dd_face_bytes(const wd_handle* h, int prec, int mu);
+
+/* Pack the faces of the packed device vector `in` (parity 1 - parity) that
+ * the neighbours' hops onto output parity `parity` need, into the device
+ * buffers send[0..7]. */
+int wd_dd_pack(wd_handle* h, int prec, int parity, const void* in, void* const send[8], void* stream);
+
+/* out = a * H_int in + b * y on the local sites of parity `parity` (y may be
+ * NULL when b = 0), H_int the hops of Eq. 1 that stay inside the sub-lattice
+ * (all of them in directions that are not split). Runs the kernels of
+ * wd_apply; it reads no face buffer, so it may overlap the exchange. */
+int wd_dd_hop_interior(wd_handle* h, int prec, int recon, int parity, const void* in, const void* y, double a,
+                       double b, void* out, void* stream);
+
+/* out += a * (hops of Eq. 1 that enter the sub-lattice through its faces),
+ * from the received face buffers recv[0..7], on the local sites of parity
+ * `parity`. After it, out = a * H in + b * y of the whole lattice restricted
+ * to this sub-lattice. */
+int wd_dd_hop_faces(wd_handle* h, int prec, int parity, const void* const recv[8], double a, void* out, void* stream);
+
+/* Local FP64 part of the dot product (a, b) = sum_i conj(a_i) b_i over the
+ * sites of one packed parity vector (Sec. 5: sums widened to FP64, the
+ * global sum across processes is the caller's FP64 allreduce). out[0], out[1]
+ * = real and imaginary part, host memory. Deterministic (fixed block order).
+ * Synchronizes `stream`. */
+int wd_vec_dot(wd_handle* h, int prec, const void* a, const void* b, double out[2], void* stream);
+
+/* y = a x + b y for packed parity vectors, a and b complex ((re, im) pairs,
+ * host memory), arithmetic as in enum wd_prec. */
+int wd_vec_axpby(wd_handle* h, int prec, const double a[2], const void* x, const double b[2], void* y,
+                 void* stream);
+
 /* Result of wd_tune. */
 typedef struct {
     int variant;          /* plain hop: kernel variant chosen (see wd_tune)                */

@@ -353,6 +353,7 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     if (!valid_prec(prec) || !valid_recon(recon) || op < WD_OP_HOP_EO || op > WD_OP_FULL || !in || !out)
         return fail(h, WD_ERR_INVALID_ARG, "wd_apply: bad argument");
     if (in == out) return fail(h, WD_ERR_INVALID_ARG, "wd_apply: in and out must not overlap");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_apply: %s", "a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     const uint4 *le, *lo;
     int rc = ensure_links(h, prec, recon, &le, &lo);
     if (rc != WD_OK) return rc;

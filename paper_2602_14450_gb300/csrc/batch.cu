@@ -16,5 +16,7 @@ extern "C" int wd_solve_batch(int n, wd_handle* const* h, const int* nrhs, const
     if (n < 1 || !h || !nrhs || !b || !x) return WD_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i)
         if (!h[i] || nrhs[i] < 0 || (nrhs[i] > 0 && (!b[i] || !x[i]))) return WD_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (h[i]->g.part) return wd::fail(h[i], WD_ERR_INVALID_ARG, "wd_solve_batch: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     return wd::solve_systems(n, h, nrhs, b, x, tol, scheme, params, per_rhs_stats, (cudaStream_t)stream);
 }

@@ -434,11 +434,15 @@ __global__ void k_build_links(Geom g, int parity, const double* U, uint4* out) {
             const int sm = cm[0] + g.L[0] * (cm[1] + g.L[1] * (cm[2] + g.L[2] * cm[3]));
             const double* uf = U + ((size_t)mu * V + s) * 18;
             const double* ub = U + ((size_t)mu * V + sm) * 18;
+            // a direction split across processes: the hops that leave the sub-lattice are
+            // remote, and their links are stored as zeros (the face terms are added apart)
+            const bool split = (g.part >> mu) & 1u;
+            const bool zf = split && c[mu] == g.L[mu] - 1, zb = split && c[mu] == 0;
             for (int e = 0; e < R; ++e) {
                 // forward: U_mu(x)[a][b]; backward: (U_mu(x-mu)^+)[a][b] = conj(U_mu(x-mu)[b][a])
                 const int a = e / 6, b = (e % 6) / 2, im = e & 1;
-                const double vf = uf[e];
-                const double vb = im ? -ub[2 * (3 * b + a) + 1] : ub[2 * (3 * b + a)];
+                const double vf = zf ? 0.0 : uf[e];
+                const double vb = zb ? 0.0 : (im ? -ub[2 * (3 * b + a) + 1] : ub[2 * (3 * b + a)]);
                 const int ef = (2 * mu) * R + e, eb = (2 * mu + 1) * R + e;
                 reinterpret_cast<T*>(out + (size_t)(ef / N) * g.Vh + h)[ef % N] = from_double<T>(vf);
                 reinterpret_cast<T*>(out + (size_t)(eb / N) * g.Vh + h)[eb % N] = from_double<T>(vb);

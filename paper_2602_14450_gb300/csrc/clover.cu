@@ -268,6 +268,7 @@ extern "C" int wd_set_clover(wd_handle* h, double csw) {
     if (!h) return WD_ERR_INVALID_ARG;
     if (!std::isfinite(csw)) return fail(h, WD_ERR_INVALID_ARG, "wd_set_clover: c_sw must be finite");
     if (!h->have_gauge) return fail(h, WD_ERR_NO_GAUGE, "wd_set_clover: wd_set_gauge has not been called");
+    if (h->g.part && csw != 0.0) return fail(h, WD_ERR_INVALID_ARG, "wd_set_clover: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     if (csw == 0.0) {
         h->have_clover = false;
         h->csw = 0.0;

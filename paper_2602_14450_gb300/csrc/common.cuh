@@ -266,6 +266,7 @@ struct Geom {
     int Vh;      // V / 2 (sites per parity)
     int bc[4];   // boundary phases, +1 or -1
     FastDiv fxh, fy, fz;   // division by Lxh, Ly, Lz
+    unsigned part;         // bit mu: direction mu is split across processes (its wrapping hops are remote)
 };
 
 // Lexicographic index of site h on parity p.

@@ -67,6 +67,9 @@ struct wd_handle {
     int tune_block[4][2][2] = {};
 
     int arith16 = 0;                   // wd_set_arith: FP16-storage hops sum in FP16 arithmetic
+
+    int dd_grid[4] = {1, 1, 1, 1};     // wd_dd_set_partition: processes per direction
+    int dd_coords[4] = {0, 0, 0, 0};   // ... and this sub-lattice's place among them
 };
 
 namespace wd {

@@ -52,6 +52,7 @@ extern "C" int wd_apply_eo_noalloc(wd_handle* h, int prec, int recon, const void
         return fail(h, WD_ERR_INVALID_ARG, "wd_apply_eo_noalloc: bad argument");
     if (in == out) return fail(h, WD_ERR_INVALID_ARG, "wd_apply_eo_noalloc: in and out must not overlap");
     if (!h->have_gauge) return fail(h, WD_ERR_NO_GAUGE, "wd_set_gauge has not been called");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_apply_eo_noalloc: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     const size_t need = vec_bytes(h, prec);
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(h, WD_ERR_INVALID_ARG,

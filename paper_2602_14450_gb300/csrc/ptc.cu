@@ -780,6 +780,7 @@ extern "C" int wd_precond_apply(wd_handle* h, int prec, const void* in, void* ou
     if (!h) return WD_ERR_INVALID_ARG;
     if ((prec != WD_FP32 && prec != WD_FP16) || !in || !out || in == out)
         return fail(h, WD_ERR_INVALID_ARG, "wd_precond_apply: bad argument");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_apply: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
     PtcBufs B;
     int rc = ptc_bufs(h, &B);
@@ -803,6 +804,7 @@ extern "C" int wd_precond_grad(wd_handle* h, int n, const float* v, const float*
                                double* loss, void* stream) {
     if (!h) return WD_ERR_INVALID_ARG;
     if (n < 1 || !v || !y || !(mu >= 0)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_grad: bad argument");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_grad: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ptc_grad(h, n, v, y, mu, loss, s);
@@ -820,6 +822,7 @@ extern "C" int wd_precond_train_step(wd_handle* h, int n, const float* v, const 
                                      double* loss, void* stream) {
     if (!h) return WD_ERR_INVALID_ARG;
     if (n < 1 || !v || !y || !(mu >= 0) || !(lr > 0)) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_train_step: bad argument");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_train_step: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     if (!h->have_precond) return fail(h, WD_ERR_INVALID_ARG, "no preconditioner weights loaded");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ptc_grad(h, n, v, y, mu, loss, s);

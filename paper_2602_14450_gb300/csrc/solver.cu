@@ -638,6 +638,7 @@ extern "C" int wd_solve(wd_handle* h, const double* b, double* x, double tol, in
                         const wd_solve_params* params, wd_solve_stats* stats, void* stream) {
     if (!h) return WD_ERR_INVALID_ARG;
     if (!b || !x) return fail(h, WD_ERR_INVALID_ARG, "wd_solve: null source or solution");
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_solve: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
     const int one = 1;
     return solve_systems(1, &h, &one, &b, &x, tol, scheme, params, stats, (cudaStream_t)stream);
 }

@@ -33,7 +33,8 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_solve_batch",
            "wd_precond_set",
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
-           "wd_last_error"]
+           "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
+           "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -98,6 +99,14 @@ def lib():
         L.wd_precond_apply.argtypes = [vp, i, vp, vp, vp]
         L.wd_precond_grad.argtypes = [vp, i, vp, vp, d, vp, C.POINTER(d), vp]
         L.wd_precond_train_step.argtypes = [vp, i, vp, vp, d, d, C.POINTER(d), vp]
+        L.wd_dd_set_partition.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.wd_dd_face_bytes.argtypes = [vp, i, i]
+        L.wd_dd_face_bytes.restype = sz
+        L.wd_dd_pack.argtypes = [vp, i, i, vp, C.POINTER(vp), vp]
+        L.wd_dd_hop_interior.argtypes = [vp, i, i, i, vp, vp, d, d, vp, vp]
+        L.wd_dd_hop_faces.argtypes = [vp, i, i, C.POINTER(vp), d, vp, vp]
+        L.wd_vec_dot.argtypes = [vp, i, vp, vp, C.POINTER(d), vp]
+        L.wd_vec_axpby.argtypes = [vp, i, C.POINTER(d), vp, C.POINTER(d), vp, vp]
         L.wd_status_string.argtypes = [i]
         L.wd_status_string.restype = C.c_char_p
         L.wd_last_error.argtypes = [vp]
@@ -199,6 +208,45 @@ class Lattice:
     def apply(self, prec, recon, op, x, y, stream=None):
         self._check(lib().wd_apply(self.h, PREC.get(prec, prec), recon, op, _ptr(x), _ptr(y), _stream(stream)),
                     "wd_apply")
+
+    # --- domain decomposition ---------------------------------------------
+    def dd_set_partition(self, grid, coords):
+        """wd_dd_set_partition: this handle is the sub-lattice at `coords` of the process grid `grid`."""
+        self._check(lib().wd_dd_set_partition(self.h, (C.c_int * 4)(*grid), (C.c_int * 4)(*coords)),
+                    "wd_dd_set_partition")
+
+    def dd_face_bytes(self, prec, mu):
+        return int(lib().wd_dd_face_bytes(self.h, PREC.get(prec, prec), int(mu)))
+
+    @staticmethod
+    def _faces(bufs):
+        return (C.c_void_p * 8)(*[None if b is None else b.data_ptr() for b in bufs])
+
+    def dd_pack(self, prec, parity, x, send, stream=None):
+        self._check(lib().wd_dd_pack(self.h, PREC.get(prec, prec), int(parity), _ptr(x), self._faces(send),
+                                     _stream(stream)), "wd_dd_pack")
+
+    def dd_hop_interior(self, prec, recon, parity, x, y, a, b, out, stream=None):
+        self._check(lib().wd_dd_hop_interior(self.h, PREC.get(prec, prec), int(recon), int(parity), _ptr(x),
+                                             None if y is None else _ptr(y), float(a), float(b), _ptr(out),
+                                             _stream(stream)), "wd_dd_hop_interior")
+
+    def dd_hop_faces(self, prec, parity, recv, a, out, stream=None):
+        self._check(lib().wd_dd_hop_faces(self.h, PREC.get(prec, prec), int(parity), self._faces(recv), float(a),
+                                          _ptr(out), _stream(stream)), "wd_dd_hop_faces")
+
+    def vec_dot(self, prec, a, b, stream=None) -> complex:
+        """wd_vec_dot: FP64 sum_i conj(a_i) b_i over one packed parity vector."""
+        out = (C.c_double * 2)()
+        self._check(lib().wd_vec_dot(self.h, PREC.get(prec, prec), _ptr(a), _ptr(b), out, _stream(stream)),
+                    "wd_vec_dot")
+        return complex(out[0], out[1])
+
+    def vec_axpby(self, prec, a, x, b, y, stream=None):
+        """wd_vec_axpby: y = a x + b y (a, b complex)."""
+        a, b = complex(a), complex(b)
+        self._check(lib().wd_vec_axpby(self.h, PREC.get(prec, prec), (C.c_double * 2)(a.real, a.imag), _ptr(x),
+                                       (C.c_double * 2)(b.real, b.imag), _ptr(y), _stream(stream)), "wd_vec_axpby")
 
     # --- learned right preconditioner -------------------------------------
     def tune(self, prec, recon, nrhs=1, stream=None):
