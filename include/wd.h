@@ -202,6 +202,18 @@ int wd_set_clover(wd_handle* h, double csw);
 int wd_set_arith(wd_handle* h, int bits);
 int wd_get_arith(const wd_handle* h);
 
+/* Limit of the bounded device-side waits (mbarrier waits on tensor-core
+ * results and on bulk copies into shared memory) of the handle's kernels, in
+ * wait rounds; rounds < 0 restores the default (4,194,304 rounds, about a
+ * second). Not a feature of the paper: it exists to exercise the timeout
+ * path, which a healthy GPU never takes. A wait that runs out raises a
+ * device flag; the kernel then waits, with the default bound, for its own
+ * copies and tensor-core operations in flight, frees its tensor memory and
+ * returns, and the call returns WD_ERR_TIMEOUT (wd_precond_apply, wd_solve,
+ * wd_solve_batch: the status of every right-hand side). rounds = 0 makes
+ * every such wait give up at once. The handle stays usable. */
+int wd_set_wait_limit(wd_handle* h, long long rounds);
+
 /* Bytes of one packed parity vector in precision `prec` (24 * V/2 reals). */
 size_t wd_vector_bytes(const wd_handle* h, int prec);
 

@@ -321,6 +321,17 @@ int wd_set_arith(wd_handle* h, int bits) {
 
 int wd_get_arith(const wd_handle* h) { return h ? (h->arith16 ? 16 : 32) : 0; }
 
+int wd_set_wait_limit(wd_handle* h, long long rounds) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (rounds >= (1LL << 31)) return fail(h, WD_ERR_INVALID_ARG, "wd_set_wait_limit: at most 2^31 - 1 rounds");
+    const unsigned w = rounds < 0 ? 0u : (unsigned)rounds + 1u;
+    if (w != h->wait_rounds) {
+        h->wait_rounds = w;
+        h->gen += 1;   // captured solver graphs hold the old limit
+    }
+    return WD_OK;
+}
+
 size_t wd_vector_bytes(const wd_handle* h, int prec) {
     if (!h || !valid_prec(prec)) return 0;
     return vec_bytes(h, prec);

@@ -68,6 +68,8 @@ struct wd_handle {
 
     int arith16 = 0;                   // wd_set_arith: FP16-storage hops sum in FP16 arithmetic
 
+    unsigned wait_rounds = 0;          // wd_set_wait_limit: rounds of a bounded device wait + 1; 0 = the default
+
     int dd_grid[4] = {1, 1, 1, 1};     // wd_dd_set_partition: processes per direction
     int dd_coords[4] = {0, 0, 0, 0};   // ... and this sub-lattice's place among them
 };
@@ -97,6 +99,7 @@ inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) 
         P.block[f] = h->tune_block[prec][recon == 12 ? 0 : 1][f];
     }
     P.arith16 = (prec == WD_FP16 && h->arith16) ? 1 : 0;
+    P.wait_rounds = h->wait_rounds;
 }
 
 }  // namespace wd

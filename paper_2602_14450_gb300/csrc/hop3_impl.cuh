@@ -64,9 +64,11 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
         : "memory");
 }
 
-// Wait for the phase of the tile; false after the iteration limit (about a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
-    for (int i = 0; i < (1 << 22); ++i) {
+// Wait for the phase of the tile; false after `limit` rounds (the default is
+// about a second; 0 gives up at once).
+constexpr unsigned MBAR_WAIT_LIMIT = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase, unsigned limit = MBAR_WAIT_LIMIT) {
+    for (unsigned i = 0; i < limit; ++i) {
         if (mbar_test(bar, phase)) return true;
         __nanosleep(64);
     }
@@ -141,10 +143,11 @@ __global__ void __launch_bounds__(128) hop3_kernel(const HopParams P, const Stag
                 bulk_copy(s_lk + (size_t)k * TS, P.links + (size_t)k * Vh + (size_t)row0 * Lxh, (unsigned)TS * 16u,
                           &bar);
         }
-        if (!mbar_wait(&bar, phase)) {
+        const bool landed = mbar_wait(&bar, phase, P.wait_rounds ? P.wait_rounds - 1 : MBAR_WAIT_LIMIT);
+        if (__syncthreads_or(!landed)) {              // uniform across the block
             if (threadIdx.x == 0 && err) atomicExch(err, 1);
-            mbar_wait(&bar, phase);                   // let the copies land before the block exits
-            return;
+            mbar_wait(&bar, phase);                   // default bound: let the copies land before the block goes on
+            break;                                    // still takes its part in the grid reduction below
         }
 
         for (int i = threadIdx.x; i < half; i += blockDim.x) {

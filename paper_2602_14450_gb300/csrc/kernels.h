@@ -40,6 +40,7 @@ struct HopParams {
     int block[2];              // threads per block, likewise; 0 = the process default
     int arith16;               // FP16 storage only: 1 = the hopping sum in FP16 arithmetic (hop16_kernel)
     int acc_exp;               // hop16_kernel: exponent of its accumulator scale (set by the launcher)
+    unsigned wait_rounds;      // limit of a bounded device wait + 1 (wd_set_wait_limit); 0 = the default limit
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.

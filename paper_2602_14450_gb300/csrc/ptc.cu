@@ -638,7 +638,8 @@ cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e,
         const long long tiles = ((long long)g.Vh + tc::TILE_M - 1) / tc::TILE_M;
         const long long tcap = (long long)num_sms() * 3;
         const int gt = (int)(tiles < tcap ? tiles : tcap);
-        k_ptc_s1_tc<__half, __half, 12><<<gt, 128, tc::SMEM_BYTES, s>>>(g, in_e, PHI, pvs, lo, V, guard, err);
+        k_ptc_s1_tc<__half, __half, 12><<<gt, 128, tc::SMEM_BYTES, s>>>(g, in_e, PHI, pvs, lo, V, guard, err,
+                                                                         h->wait_rounds);
         k_ptc_s2_pf<__half, __nv_bfloat16, __half, __half><<<g2, 128, 0, s>>>(g, in_e, PHI, pvs, out_e, le, V, guard);
     } else {
         const long long pvs = (long long)spinor_units(WD_BF16) * g.Vh;

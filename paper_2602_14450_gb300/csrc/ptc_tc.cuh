@@ -39,7 +39,7 @@ constexpr int A_TILE_BYTES = TILE_M * K * 2; // one colour's operand tile (16 KB
 constexpr int B_BYTES = N * K * 2;           // 8 KB
 constexpr int SMEM_BYTES = 3 * A_TILE_BYTES + B_BYTES + 64;
 constexpr int TMEM_COLS = 64;
-constexpr unsigned WAIT_LIMIT = 1u << 22;    // try_wait rounds before giving up
+constexpr unsigned WAIT_LIMIT = 1u << 22;    // try_wait rounds before giving up (the default)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -80,10 +80,11 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false when the bound ran out.
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false when `limit`
+// try_wait rounds ran out (limit 0: give up at once, without a round).
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, unsigned limit = WAIT_LIMIT) {
     const uint32_t a = smem_addr(bar);
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i) {
+    for (unsigned i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -121,7 +122,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 template <typename TIN, typename LT, int R>
 __global__ void __launch_bounds__(128, 3) k_ptc_s1_tc(Geom g, const uint4* in_e, uint4* phi, long long pvs,
                                                       const uint4* links_o, const float2* V, const SolverState* guard,
-                                                      int* err) {
+                                                      int* err, unsigned wait_rounds) {
+    // wait_rounds = the limit of the MMA waits + 1; 0 = the default limit
+    const unsigned limit = wait_rounds ? wait_rounds - 1 : tc::WAIT_LIMIT;
     using namespace tc;
     if (guarded(guard, GUARD_INNER)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(128, 3) k_ptc_s1_tc(Geom g, const uint4* in_e,
                 }
                 mma_commit(bar);
             }
-            const bool landed = bar_wait(bar, phase);
+            const bool landed = bar_wait(bar, phase, limit);
             failed = __syncthreads_or(!landed);     // uniform across the CTA
             if (failed) {                           // `phase` stays the one still pending
                 if (tid == 0 && err) atomicExch(err, 1);
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(128, 3) k_ptc_s1_tc(Geom g, const uint4* in_e,
             fence_after();
         }
     }
-    if (failed && tid == 0) bar_wait(bar, phase);   // bounded: let an MMA still in flight finish
+    if (failed && tid == 0) bar_wait(bar, phase);   // default bound: let an MMA still in flight finish
     fence_before();
     __syncthreads();
     fence_after();

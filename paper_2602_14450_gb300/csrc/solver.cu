@@ -109,15 +109,17 @@ static int prepare(Sys& S, int prec, int recon_lo, bool learned) {
         *flo[i] = (uint4*)workspace(h, pre + nlo[i], blo);
         if (!*flo[i]) return fail(h, WD_ERR_CUDA, "out of device memory (%s)", nlo[i]);
     }
+    // raised by any kernel of the solve whose bounded device wait gave up
+    S.err = ptc_err(h);
+    if (!S.err) return fail(h, WD_ERR_CUDA, "out of device memory");
+    if (cudaMemset(S.err, 0, sizeof(int)) != cudaSuccess) return fail(h, WD_ERR_CUDA, "cudaMemset");
     if (learned) {
         S.phat = (uint4*)workspace(h, pre + "phat", blo);
         S.shat = (uint4*)workspace(h, pre + "shat", blo);
         S.PHI = ptc_phi16(h);
         S.V = ptc_collapsed(h);
-        S.err = ptc_err(h);
-        if (!S.phat || !S.shat || !S.PHI || !S.V || !S.err)
+        if (!S.phat || !S.shat || !S.PHI || !S.V)
             return fail(h, WD_ERR_CUDA, "out of device memory (preconditioner)");
-        if (cudaMemset(S.err, 0, sizeof(int)) != cudaSuccess) return fail(h, WD_ERR_CUDA, "cudaMemset");
     }
     const size_t lexb = (size_t)S.nrhs * 2 * h->g.Vh * 24 * sizeof(double);
     S.bl = const_cast<double*>(S.b);
@@ -140,6 +142,8 @@ static HopParams hop_params(const Sys& S, int stage, int guard_kind) {
     P.rc = red_ctx(S.h, stage);
     P.guard = S.h->st;
     P.guard_kind = guard_kind;
+    P.wait_rounds = S.h->wait_rounds;
+    P.err = S.err;
     return P;
 }
 
@@ -560,7 +564,7 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
     }
     WD_CUDA(h0, cudaEventRecord(h0->t1, s));
     if ((rc = read_states(sys, s)) != WD_OK) return rc;
-    bool timed_out = false;   // a bounded device wait of the preconditioner gave up
+    bool timed_out = false;   // a bounded device wait of a kernel gave up
     for (auto& S : sys) {
         if (!S.err) continue;
         int herr = 0;

@@ -34,7 +34,7 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_precond_set",
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
-           "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby"]
+           "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -83,6 +83,7 @@ def lib():
         L.wd_set_clover.argtypes = [vp, d]
         L.wd_set_arith.argtypes = [vp, i]
         L.wd_get_arith.argtypes = [vp]
+        L.wd_set_wait_limit.argtypes = [vp, C.c_longlong]
         L.wd_vector_bytes.argtypes = [vp, i]
         L.wd_vector_bytes.restype = sz
         L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
@@ -183,6 +184,10 @@ class Lattice:
     def set_arith(self, bits):
         """wd_set_arith: arithmetic of the FP16-storage hopping term, 32 (FP32) or 16 (FP16, half2)."""
         self._check(lib().wd_set_arith(self.h, int(bits)), "wd_set_arith")
+
+    def set_wait_limit(self, rounds):
+        """wd_set_wait_limit: rounds of every bounded device wait (< 0: the default)."""
+        self._check(lib().wd_set_wait_limit(self.h, int(rounds)), "wd_set_wait_limit")
 
     @property
     def arith(self):
