@@ -230,6 +230,25 @@ int wd_unpack(wd_handle* h, int prec, int parity, const void* packed, double* le
  * (in and out must not overlap). Arithmetic as in enum wd_prec. */
 int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* out, void* stream);
 
+/* wd_apply on nrhs right-hand sides at once: `in` and `out` hold nrhs packed
+ * vectors of the operator's kind (parity vectors, or full vectors for
+ * WD_OP_FULL) back to back, right-hand side r at r times the vector size. The
+ * kernels serve all right-hand sides in one launch per hop (the batched form
+ * of the 12 spin-colour sources); with FP16 arithmetic each thread may apply
+ * its site's links to K right-hand sides (wd_tune, wd_set_rhs_per_thread).
+ * 1 <= nrhs <= 1024. */
+int wd_apply_batch(wd_handle* h, int prec, int recon, int op, int nrhs, const void* in, void* out, void* stream);
+
+/* Right-hand sides per thread of the FP16-arithmetic hop (wd_set_arith(16),
+ * FP16 storage) with link format `recon`, as wd_tune would choose them:
+ * k_plain for the plain hop, k_reducing for the hop with fused epilogue and
+ * dot products (1..12; a batch uses the largest divisor of its nrhs up to
+ * k), links_smem = 1 to stage the site's links in shared memory instead of
+ * registers. The results are the same bits for every k (each right-hand
+ * side is computed by the same operations); only the speed differs. Not a
+ * feature of the paper. */
+int wd_set_rhs_per_thread(wd_handle* h, int recon, int k_plain, int k_reducing, int links_smem);
+
 /* out = in - kappa^2 H_eo H_oe in, exactly as wd_apply(h, prec, recon,
  * WD_OP_EO_A, ...), for callers that must not allocate device memory (code
  * that runs under a caching allocator owning all device memory, or code that
@@ -336,6 +355,16 @@ typedef struct {
     int variant_reducing; /* hop with fused epilogue and dot products: variant chosen      */
     int block_reducing;   /* ... threads per block chosen                                  */
     double us_reducing;   /* ... its average launch time, microseconds                     */
+    /* FP16 storage with FP16 arithmetic (wd_set_arith(16)) and nrhs > 1: the FP16-arithmetic
+       hop over K right-hand sides per thread (the site's links loaded once for K), K a divisor of
+       nrhs up to 12, links in registers or shared memory; 1, 0, 0 otherwise                  */
+    int rhs_per_thread;           /* plain hop: K chosen                                       */
+    int rhs_links_smem;           /* plain hop: 1 = links staged in shared memory             */
+    double us16;                  /* plain hop: its average launch time, microseconds         */
+    int rhs_per_thread_reducing;  /* hop with fused epilogue and dot products: K chosen       */
+    int rhs_links_smem_reducing;  /* ... links in shared memory                               */
+    double us16_reducing;         /* ... its average launch time, microseconds                */
+    int candidates16;             /* FP16-arithmetic configurations timed per form            */
 } wd_tune_result;
 
 /* Autotune the hopping kernel H_eo (Eq. 1) of storage precision `prec` with
@@ -351,11 +380,15 @@ typedef struct {
  * thread, FP32x2; not FP64),
  * and for 16-bit storage 3 (tiles staged in shared memory), 6 (FP32x2 column
  * pairs; 64, 128 threads, and 256 for BF16) and, with 12-real links, 5 (per-thread cp.async
- * ring). These are the kernels of FP32 arithmetic; with wd_set_arith(16)
- * the FP16 hops use the FP16-arithmetic kernel, whose shape is fixed (one
- * site per thread, 128 threads), whatever the tuning. Not a feature of the
- * paper. Synchronizes `stream`; allocates two scratch vectors of nrhs parity
- * vectors. `out` may be NULL. */
+ * ring). These are the kernels of FP32 arithmetic. With wd_set_arith(16) and
+ * FP16 storage the FP16-arithmetic kernel runs instead (128 threads, one site
+ * per thread); for nrhs > 1 wd_tune then also times it with K right-hand
+ * sides per thread (every divisor K of nrhs up to 12; the site's 8 links are
+ * loaded once for its K right-hand sides, in registers or in shared memory)
+ * and keeps the fastest K for each form (wd_set_rhs_per_thread sets them
+ * directly); a batch of nrhs right-hand sides then uses the largest divisor
+ * of nrhs up to that K. Not a feature of the paper. Synchronizes `stream`;
+ * allocates three scratch vectors of nrhs parity vectors. `out` may be NULL. */
 int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream, wd_tune_result* out);
 
 /* Fill `p` with the defaults of `scheme` (Table 2 rows; s = 128, sigma = 64

@@ -359,25 +359,28 @@ int wd_unpack(wd_handle* h, int prec, int parity, const void* packed, double* le
     return e == cudaSuccess ? WD_OK : cuda_fail(h, e, "wd_unpack");
 }
 
-int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* out, void* stream) {
-    if (!h) return WD_ERR_INVALID_ARG;
-    if (!valid_prec(prec) || !valid_recon(recon) || op < WD_OP_HOP_EO || op > WD_OP_FULL || !in || !out)
-        return fail(h, WD_ERR_INVALID_ARG, "wd_apply: bad argument");
-    if (in == out) return fail(h, WD_ERR_INVALID_ARG, "wd_apply: in and out must not overlap");
-    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "wd_apply: %s", "a split lattice (wd_dd_set_partition) has only the wd_dd_* operators");
+// The operators of wd_apply on nrhs packed vectors stored back to back.
+static int apply_n(wd_handle* h, int prec, int recon, int op, int nrhs, const void* in, void* out, void* stream,
+                   const char* who) {
+    if (!valid_prec(prec) || !valid_recon(recon) || op < WD_OP_HOP_EO || op > WD_OP_FULL || !in || !out ||
+        nrhs < 1)
+        return fail(h, WD_ERR_INVALID_ARG, "%s: bad argument", who);
+    if (in == out) return fail(h, WD_ERR_INVALID_ARG, "%s: in and out must not overlap", who);
+    if (h->g.part) return fail(h, WD_ERR_INVALID_ARG, "%s: a split lattice (wd_dd_set_partition) has only the wd_dd_* operators", who);
     const uint4 *le, *lo;
     int rc = ensure_links(h, prec, recon, &le, &lo);
     if (rc != WD_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t half = vec_bytes(h, prec);
+    const long long vsu = (long long)spinor_units(prec) * h->g.Vh;   // units of one parity vector
     HopParams P{};
     P.g = h->g;
     P.rc.partials = nullptr;
     P.rc.ticket = nullptr;
     P.rc.st = nullptr;
     P.rc.stage = ST_NONE;
-    P.nrhs = 1;
-    P.vs = 0;
+    P.nrhs = nrhs;
+    P.vs = op == WD_OP_FULL ? 2 * vsu : vsu;
     P.guard = nullptr;
     P.guard_kind = GUARD_NONE;
     apply_tuning(h, prec, recon, P);
@@ -410,7 +413,7 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
     case WD_OP_HOP_EO: e = hop(0, in, out, EPI_H, 1.0, 0.0, nullptr); break;
     case WD_OP_HOP_OE: e = hop(1, in, out, EPI_H, 1.0, 0.0, nullptr); break;
     case WD_OP_EO_A: {   // with clover: in - kappa^2 C_ee^-1 H_eo C_oo^-1 H_oe in (Eq. 4)
-        void* tmp = workspace(h, "apply.tmp." + std::to_string(prec), half);
+        void* tmp = workspace(h, "apply.tmp." + std::to_string(prec), half * (size_t)nrhs);
         if (!tmp) return fail(h, WD_ERR_CUDA, "out of device memory");
         e = hop(1, in, tmp, EPI_H, 1.0, 0.0, nullptr, ci_o);
         if (e == cudaSuccess) e = hop(0, tmp, out, EPI_Y, -k * k, 1.0, in, ci_e);
@@ -424,9 +427,10 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
         if (cf_e) {   // out = C in first, then the hop adds to it in place
             e = by_prec(prec, [&](auto tag) {
                 typedef typename decltype(tag)::type T;
-                cudaError_t r2 = Ops<T>::apply_mat(h->g.Vh, 1, 0, cf_e, (const uint4*)ie, (uint4*)oe, s);
+                cudaError_t r2 = Ops<T>::apply_mat(h->g.Vh, nrhs, 2 * vsu, cf_e, (const uint4*)ie, (uint4*)oe, s);
                 if (r2 == cudaSuccess)
-                    r2 = Ops<T>::apply_mat(h->g.Vh, 1, 0, cf_o, (const uint4*)(ie + half), (uint4*)(oe + half), s);
+                    r2 = Ops<T>::apply_mat(h->g.Vh, nrhs, 2 * vsu, cf_o, (const uint4*)(ie + half),
+                                           (uint4*)(oe + half), s);
                 return r2;
             });
             ye = oe;
@@ -437,7 +441,31 @@ int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* ou
         break;
     }
     }
-    return e == cudaSuccess ? WD_OK : cuda_fail(h, e, "wd_apply");
+    return e == cudaSuccess ? WD_OK : cuda_fail(h, e, who);
+}
+
+int wd_apply(wd_handle* h, int prec, int recon, int op, const void* in, void* out, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    return apply_n(h, prec, recon, op, 1, in, out, stream, "wd_apply");
+}
+
+int wd_apply_batch(wd_handle* h, int prec, int recon, int op, int nrhs, const void* in, void* out, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (nrhs < 1 || nrhs > 1024) return fail(h, WD_ERR_INVALID_ARG, "wd_apply_batch: nrhs must be 1..1024");
+    return apply_n(h, prec, recon, op, nrhs, in, out, stream, "wd_apply_batch");
+}
+
+int wd_set_rhs_per_thread(wd_handle* h, int recon, int k_plain, int k_reducing, int links_smem) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!valid_recon(recon) || k_plain < 1 || k_plain > 12 || k_reducing < 1 || k_reducing > 12 ||
+        (links_smem != 0 && links_smem != 1))
+        return fail(h, WD_ERR_INVALID_ARG, "wd_set_rhs_per_thread: bad argument");
+    const int ri = recon == 12 ? 0 : 1;
+    h->tune_rhs[ri][0] = k_plain;
+    h->tune_rhs[ri][1] = k_reducing;
+    h->tune_rhs_smem[ri][0] = h->tune_rhs_smem[ri][1] = links_smem;
+    h->gen += 1;   // captured solver graphs hold the old kernels
+    return WD_OK;
 }
 
 const char* wd_status_string(int status) {

@@ -65,6 +65,9 @@ struct wd_handle {
     // hop kernel chosen by wd_tune per [prec][recon 12 -> 0, 18 -> 1][without / with fused reduction]; 0 = default
     int tune_variant[4][2][2] = {};
     int tune_block[4][2][2] = {};
+    // FP16-arithmetic hop chosen by wd_tune: right-hand sides per thread and links in shared memory
+    int tune_rhs[2][2] = {};
+    int tune_rhs_smem[2][2] = {};
 
     int arith16 = 0;                   // wd_set_arith: FP16-storage hops sum in FP16 arithmetic
 
@@ -100,6 +103,10 @@ inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) 
     }
     P.arith16 = (prec == WD_FP16 && h->arith16) ? 1 : 0;
     P.wait_rounds = h->wait_rounds;
+    for (int f = 0; f < 2; ++f) {
+        P.rhs_group[f] = P.arith16 ? h->tune_rhs[recon == 12 ? 0 : 1][f] : 0;
+        P.rhs_smem[f] = P.arith16 ? h->tune_rhs_smem[recon == 12 ? 0 : 1][f] : 0;
+    }
 }
 
 }  // namespace wd

@@ -84,12 +84,12 @@ __device__ __forceinline__ void project16(int mu, bool fwd, const uint4 (&u)[3],
     }
 }
 
-// x[k * 3 + a] = sum_b M_ab h[k * 3 + b] for link j of a group of units
-// (word j * R / 2 + 3 a + b holds M_ab; R = 12: row 2 = conj(row0 x row1)).
+// The 3x3 link j of a group of units as 9 half2 words, m[3 a + b] = M_ab
+// (word j * R / 2 + 3 a + b of the group; R = 12: row 2 = conj(row0 x row1),
+// rebuilt in FP16).
 template <int R, int GU>
-__device__ __forceinline__ void link_mul16(const uint4 (&u)[GU], int j, const __half2 (&h)[6], __half2 (&x)[6]) {
+__device__ __forceinline__ void link_load16(const uint4 (&u)[GU], int j, __half2 (&m)[9]) {
     constexpr int W = R / 2;
-    __half2 m[9];
 #pragma unroll
     for (int e = 0; e < W; ++e) m[e] = as_h2(word_of(u[(j * W + e) >> 2], (j * W + e) & 3));
     if (R == 12) {
@@ -104,6 +104,10 @@ __device__ __forceinline__ void link_mul16(const uint4 (&u)[GU], int j, const __
             m[6 + b] = as_h2(as_w(z) ^ 0x80000000u);                               // conjugate
         }
     }
+}
+
+// x[k * 3 + a] = sum_b M_ab h[k * 3 + b] for a link given as m[3 a + b].
+__device__ __forceinline__ void mul16(const __half2 (&m)[9], const __half2 (&h)[6], __half2 (&x)[6]) {
     __half2 ih[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) ih[i] = times_i(h[i]);
@@ -115,6 +119,14 @@ __device__ __forceinline__ void link_mul16(const uint4 (&u)[GU], int j, const __
             z = cmac16(m[3 * a + 1], h[3 * k + 1], ih[3 * k + 1], z);
             x[3 * k + a] = cmac16(m[3 * a + 2], h[3 * k + 2], ih[3 * k + 2], z);
         }
+}
+
+// x[k * 3 + a] = sum_b M_ab h[k * 3 + b] for link j of a group of units.
+template <int R, int GU>
+__device__ __forceinline__ void link_mul16(const uint4 (&u)[GU], int j, const __half2 (&h)[6], __half2 (&x)[6]) {
+    __half2 m[9];
+    link_load16<R, GU>(u, j, m);
+    mul16(m, h, x);
 }
 
 // acc (word 3 s + c) += f * (rebuilt four-spinor of chi); fb = bits of (f, f).

@@ -41,6 +41,9 @@ struct HopParams {
     int arith16;               // FP16 storage only: 1 = the hopping sum in FP16 arithmetic (hop16_kernel)
     int acc_exp;               // hop16_kernel: exponent of its accumulator scale (set by the launcher)
     unsigned wait_rounds;      // limit of a bounded device wait + 1 (wd_set_wait_limit); 0 = the default limit
+    int rhs_group[2];          // FP16 arithmetic: right-hand sides per thread (hop16m_kernel) without / with a
+                               // fused reduction; 0 or 1 = one (hop16_kernel); must divide nrhs to be used
+    int rhs_smem[2];           // ... and 1 = the site's links in shared memory instead of registers
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.

@@ -10,6 +10,7 @@
 #include "blas_impl.cuh"
 #include "hop2_impl.cuh"
 #include "hop16_impl.cuh"
+#include "hop16m_impl.cuh"
 #include "hop3_impl.cuh"
 #include "hop_impl.cuh"
 #include "kernels.h"
@@ -94,6 +95,32 @@ bool stage_geom(const Geom& g, StageGeom* sg, size_t* smem) {
     return *smem <= 113 * 1024;
 }
 
+// The FP16-arithmetic hop over groups of K right-hand sides per thread.
+template <int R, int E, int D, bool LSM>
+cudaError_t run_hop16m(const HopParams& Q, int K, cudaStream_t s) {
+    constexpr int blk = Hop16mShape<R>::THREADS;
+    const void* k = (const void*)hop16m_kernel<R, E, D, LSM>;
+    const size_t smem = hop16m_smem<R, D, LSM>(K);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (smem > 96 * 1024) return cudaErrorInvalidValue;
+    const int groups = Q.nrhs / K;
+    long nb = ((long)Q.g.Vh + blk - 1) / blk;
+    if (D != RED_NONE) {   // one resident wave, at most MAX_RED_BLOCKS partial sums per right-hand side
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, blk, smem) != cudaSuccess || per < 1) per = 1;
+        long wave = (long)per * num_sms() / groups;
+        if (nb > wave) nb = wave;
+        if (nb > MAX_RED_BLOCKS) nb = MAX_RED_BLOCKS;
+    }
+    if (nb < 1) nb = 1;
+    return launch_k(hop16m_kernel<R, E, D, LSM>, nb * groups, blk, smem, s, Q);
+}
+
 template <typename T, int R, int E, int D>
 cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
     if constexpr (std::is_same<T, __half>::value) {
@@ -101,6 +128,16 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
             constexpr int blk = Hop16Bounds<R, D, false, 2>::THREADS;
             HopParams Q = P;
             Q.acc_exp = acc_exponent(P.a);
+            constexpr int form = D == RED_NONE ? 0 : 1;
+            int K = P.rhs_group[form] < 12 ? P.rhs_group[form] : 12;
+            while (K > 1 && P.nrhs % K) --K;                       // the largest divisor of nrhs up to the choice
+            if (K > 1 && !P.mat) {                                 // several right-hand sides per thread
+                Q.rhs_group[form] = K;
+                const cudaError_t le_ = P.rhs_smem[form] ? run_hop16m<R, E, D, true>(Q, K, s)
+                                                         : run_hop16m<R, E, D, false>(Q, K, s);
+                if (le_ != cudaSuccess) return le_;
+                return cudaGetLastError();
+            }
             if (P.mat) {
                 const void* km = (const void*)hop16_kernel<R, E, D, true, 1>;
                 const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(km, P.g.Vh, blk, P.nrhs);

@@ -94,10 +94,53 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
             }
         }
     }
+    // FP16 arithmetic (wd_set_arith(16)): right-hand sides per thread of the FP16-arithmetic hop, K dividing
+    // nrhs (K = 1: one per thread), the site's links in registers or in shared memory
+    const int ri = recon == 12 ? 0 : 1;
+    int best_k[2] = {1, 1}, best_lsm[2] = {0, 0};
+    float best16[2] = {1e30f, 1e30f};
+    int cands16 = 0;
+    if (prec == WD_FP16 && h->arith16 && err == cudaSuccess) {
+        P.arith16 = 1;
+        P.variant[0] = P.variant[1] = 0;
+        P.block[0] = P.block[1] = 0;
+        for (int form = 0; form < 2 && err == cudaSuccess; ++form) {
+            for (int k = 1; k <= 12 && err == cudaSuccess; ++k) {
+                if (nrhs % k) continue;
+                for (int lsm = 0; lsm < (k > 1 ? 2 : 1) && err == cudaSuccess; ++lsm) {
+                    P.rhs_group[form] = k;
+                    P.rhs_smem[form] = lsm;
+                    auto launch = [&]() {
+                        return form == 0 ? Ops<__half>::hop(recon, EPI_H, RED_NONE, P, s)
+                                         : Ops<__half>::hop(recon, EPI_Y, RED_TS, P, s);
+                    };
+                    for (int i = 0; i < 2 && err == cudaSuccess; ++i) err = launch();
+                    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+                    for (int i = 0; i < 8 && err == cudaSuccess; ++i) err = launch();
+                    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+                    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                    if (err != cudaSuccess) break;
+                    ms /= 8.f;
+                    if (form == 0) ++cands16;
+                    if (ms < best16[form]) {
+                        best16[form] = ms;
+                        best_k[form] = k;
+                        best_lsm[form] = lsm;
+                    }
+                }
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(h, err, "wd_tune: timing a candidate");
-    const int ri = recon == 12 ? 0 : 1;
+    if (prec == WD_FP16 && h->arith16)
+        for (int form = 0; form < 2; ++form) {
+            h->tune_rhs[ri][form] = best_k[form];
+            h->tune_rhs_smem[ri][form] = best_lsm[form];
+        }
     for (int form = 0; form < 2; ++form) {
         h->tune_variant[prec][ri][form] = best[form].variant;
         h->tune_block[prec][ri][form] = best[form].block;
@@ -112,6 +155,14 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
         out->variant_reducing = best[1].variant;
         out->block_reducing = best[1].block;
         out->us_reducing = 1e3 * best_ms[1];
+        const bool a16 = prec == WD_FP16 && h->arith16;
+        out->rhs_per_thread = a16 ? best_k[0] : 1;
+        out->rhs_links_smem = a16 ? best_lsm[0] : 0;
+        out->us16 = a16 ? 1e3 * best16[0] : 0.0;
+        out->rhs_per_thread_reducing = a16 ? best_k[1] : 1;
+        out->rhs_links_smem_reducing = a16 ? best_lsm[1] : 0;
+        out->us16_reducing = a16 ? 1e3 * best16[1] : 0.0;
+        out->candidates16 = cands16;
     }
     return WD_OK;
 }

@@ -34,7 +34,8 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_precond_set",
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
-           "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit"]
+           "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit", "wd_apply_batch",
+           "wd_set_rhs_per_thread"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -43,7 +44,9 @@ PRECOND_FLOATS = 6912
 class TuneResult(C.Structure):
     _fields_ = [("variant", C.c_int), ("block", C.c_int), ("us", C.c_double), ("default_us", C.c_double),
                 ("candidates", C.c_int), ("variant_reducing", C.c_int), ("block_reducing", C.c_int),
-                ("us_reducing", C.c_double)]
+                ("us_reducing", C.c_double), ("rhs_per_thread", C.c_int), ("rhs_links_smem", C.c_int),
+                ("us16", C.c_double), ("rhs_per_thread_reducing", C.c_int), ("rhs_links_smem_reducing", C.c_int),
+                ("us16_reducing", C.c_double), ("candidates16", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -90,6 +93,8 @@ def lib():
         L.wd_unpack.argtypes = [vp, i, i, vp, vp, vp]
         L.wd_apply.argtypes = [vp, i, i, i, vp, vp, vp]
         L.wd_apply_eo_noalloc.argtypes = [vp, i, i, vp, vp, vp]
+        L.wd_apply_batch.argtypes = [vp, i, i, i, i, vp, vp, vp]
+        L.wd_set_rhs_per_thread.argtypes = [vp, i, i, i, i]
         L.wd_tune.argtypes = [vp, i, i, i, vp, C.POINTER(TuneResult)]
         L.wd_solve_params_default.argtypes = [i, C.POINTER(SolveParams)]
         L.wd_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]
@@ -214,6 +219,17 @@ class Lattice:
         self._check(lib().wd_apply(self.h, PREC.get(prec, prec), recon, op, _ptr(x), _ptr(y), _stream(stream)),
                     "wd_apply")
 
+    def apply_batch(self, prec, recon, op, nrhs, x, y, stream=None):
+        """wd_apply_batch: the operator on nrhs packed vectors stored back to back."""
+        self._check(lib().wd_apply_batch(self.h, PREC.get(prec, prec), recon, op, int(nrhs), _ptr(x), _ptr(y),
+                                         _stream(stream)), "wd_apply_batch")
+
+    def set_rhs_per_thread(self, recon, k_plain, k_reducing=None, links_smem=0):
+        """wd_set_rhs_per_thread: right-hand sides per thread of the FP16-arithmetic hop."""
+        k_reducing = k_plain if k_reducing is None else k_reducing
+        self._check(lib().wd_set_rhs_per_thread(self.h, int(recon), int(k_plain), int(k_reducing), int(links_smem)),
+                    "wd_set_rhs_per_thread")
+
     # --- domain decomposition ---------------------------------------------
     def dd_set_partition(self, grid, coords):
         """wd_dd_set_partition: this handle is the sub-lattice at `coords` of the process grid `grid`."""
@@ -259,9 +275,7 @@ class Lattice:
         r = TuneResult()
         self._check(lib().wd_tune(self.h, PREC.get(prec, prec), int(recon), int(nrhs), _stream(stream), C.byref(r)),
                     "wd_tune")
-        return {"variant": r.variant, "block": r.block, "us": r.us, "default_us": r.default_us,
-                "candidates": r.candidates, "variant_reducing": r.variant_reducing,
-                "block_reducing": r.block_reducing, "us_reducing": r.us_reducing}
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def precond_set(self, w):
         """w: float32 tensor of PRECOND_FLOATS weights (flat layout of wd.h), CPU or CUDA."""
