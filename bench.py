@@ -305,6 +305,12 @@ def main():
     for prec, recon in (("fp16", 12), ("fp16", 18), ("fp16a", 12), ("fp16a", 18), ("fp32", 12), ("fp32", 18),
                         ("fp64", 18)):
         sweep[f"{prec}_{recon}"] = dslash_bench.hop_timing(lat, prec, recon, args.dslash_launches, stream)
+    # arithmetic roofs: GB300's FP64 pipe bounds the FP64 hop (1320 flops per site: 6 x 168 + 2 x 156, the
+    # count of the oracle's instrumented three-step hop in this Dirac basis)
+    fma_peaks = {f"fp{b}": wd.fma_peak(b, stream=stream) for b in (64, 32, 16)}
+    f64 = sweep["fp64_18"]
+    f64["tflops"] = 1320 * f64["sites"] / (f64["us"] * 1e-6) / 1e12
+    f64["frac_of_measured_fp64_fma_peak"] = f64["tflops"] / fma_peaks["fp64"]
     peak, peak_kind = measured_peaks()
     top = sweep["fp16a_12" if args.arith == 16 else "fp16_12"]
     roof = {"bound": "hbm", "achieved": top["gbs"], "peak": peak, "unit": "GB/s", "frac": top["gbs"] / peak,
@@ -321,6 +327,11 @@ def main():
         studies_out["batched"] = studies.batched(workloads.KAPPA["16x16x16x32"], TOL, stream, args.arith)
         studies_out["learned"] = studies.learned_preconditioner(wl.kappa, lat, b, TOL, stream)
         studies_out["tableau"] = studies.tableau(workloads.KAPPA["16x16x16x32"], TOL, stream, arith=args.arith)
+        studies_out["tableau_ftz"] = studies.tableau(workloads.KAPPA["16x16x16x32"], TOL, stream, arith=args.arith,
+                                                     ftz=1, extras=False)
+        if args.workload in workloads.KAPPA_HARD:
+            studies_out["harder_system"] = studies.harder_system(wl, workloads.KAPPA_HARD[args.workload], TOL, stream,
+                                                                 args.arith, u=u)
         studies_out["table2"] = studies.table2(lat, 1e-13, stream)
         studies_out["clover"] = studies.clover(wl, 1.0, TOL, stream, args.arith)
 
@@ -342,6 +353,7 @@ def main():
         "forms": forms,
         "speedup_vs_fp64": (forms["fp64"]["time_s"] / forms["mixed_fp16"]["time_s"]) if "fp64" in forms else None,
         "dslash_sweep": sweep,
+        "fma_peaks_tflops": fma_peaks,
         "tuning": tuning,
         "solve": st.as_dict(),
         **studies_out,

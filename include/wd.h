@@ -453,6 +453,16 @@ int wd_precond_grad(wd_handle* h, int n, const float* v, const float* y, double 
 int wd_precond_train_step(wd_handle* h, int n, const float* v, const float* y, double mu, double lr, double* loss,
                           void* stream);
 
+/* Arithmetic throughput probe (not a feature of the paper): launches one
+ * kernel on `stream` that runs `iters` steps of 8 independent fused
+ * multiply-add chains per thread on the FP64 (bits = 64), FP32 (32) or
+ * packed FP16 (16) pipe, over 8 blocks of 256 threads per SM, and stores in
+ * *flops the floating-point operations of the launch (2 per multiply-add and
+ * lane). The caller times the launch (CUDA events on `stream`) to get the
+ * rate that bounds a kernel limited by that pipe. `sink`: a device buffer of
+ * at least 4 * 8 * SMs bytes the kernel may write. */
+int wd_fma_probe(int bits, long long iters, void* sink, void* stream, double* flops);
+
 /* Human-readable name of a status code (static string). */
 const char* wd_status_string(int status);
 

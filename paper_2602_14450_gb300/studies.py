@@ -128,6 +128,29 @@ def learned_preconditioner(kappa: float, test_lat: "wd.Lattice", b: torch.Tensor
     }
 
 
+def harder_system(wl, kappa: float, tol: float = 1e-10, stream=None, arith: int = 16, u=None) -> dict:
+    """The FP16-mixed solve (Alg. 3 + Alg. 4) against FP64 BiCGStab on the
+    workload's lattice, links and source at a larger kappa (a system closer to
+    critical, as hard as the paper's in FP64 matvecs): times and counts."""
+    stream = stream or torch.cuda.current_stream()
+    lat = wd.Lattice(wl.dims, kappa)
+    lat.set_gauge(torch.view_as_real(wl.gauge() if u is None else u).contiguous())
+    lat.set_arith(arith)
+    b = synth.to_host_layout(wl.source()).cuda()
+    x = torch.zeros_like(b)
+    out = {"kappa": kappa, "lattice": list(wl.dims), "arith": arith}
+    for scheme in ("mixed_fp16", "fp64"):
+        q = wd.default_params(scheme)
+        q.max_inner, q.max_outer = 4, 1
+        lat.solve(b, x.zero_(), tol, scheme, q, stream=stream, check=False)   # links, workspaces, graphs
+        st, t = _timed(lambda: lat.solve(b, x.zero_(), tol, scheme, stream=stream, check=False), stream)
+        out[scheme] = {"time_s": t, "inner_matvecs": st.inner_matvecs, "outer_iterations": st.outer_iterations,
+                       "true_residual": st.true_residual, "status": st.status}
+    out["speedup_vs_fp64"] = out["fp64"]["time_s"] / out["mixed_fp16"]["time_s"]
+    lat.close()
+    return out
+
+
 def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 40) -> dict:
     """The rows of Table 2 on a lattice with the paper's source b = (1, 0, ..., 0)
     (unit real entry at even site 0, spin 0, colour 0) and its stopping rule
@@ -167,7 +190,7 @@ def table2(lat: "wd.Lattice", tol: float = 1e-13, stream=None, max_outer: int = 
 
 def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 128.0, 1024.0, 4096.0),
             sigma_values=(0.0, 1.0, 16.0, 64.0, 256.0, 1024.0), max_outer: int = 30, source: str = "point",
-            arith: int = 32) -> dict:
+            arith: int = 32, ftz: int = 0, extras: bool = True) -> dict:
     """FP16 low-precision matvecs to 1e-10 over the Alg. 3 scale s and the Alg. 4
     residual norm sigma (sigma = 0: no inner rescaling), recalculated gamma, on
     the 16^3 x 32 workload with the paper's unit source (or the Gaussian one)
@@ -176,7 +199,10 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
     (Alg. 5, sigma_lambda = sigma) on/off at s = 128, sigma = 64, and Alg. 2
     with unrescaled FP16 (the paper's unimproved case). Inner solves stop at 2000
     matvecs and the refinement at max_outer trips; runs that stop at the caps
-    report their status and the matvecs spent."""
+    report their status and the matvecs spent. With ftz every low-precision
+    store flushes subnormal values to zero, the regime of the paper's build
+    (-Ofast implies -Kfz, Sec. 6); extras = False skips the corners and the
+    comparison forms."""
     stream = stream or torch.cuda.current_stream()
     dims = (16, 16, 16, 32)
     lat = _lattice(dims, kappa, SMEARED_SEED, arith)
@@ -191,6 +217,7 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
         p.max_outer = max_outer
         if scheme != "fp64":
             p.max_inner = 2000          # bounds the work of settings that crawl
+        p.ftz = ftz
         for k, v in kw.items():
             setattr(p, k, v)
         st = lat.solve(b, x.zero_(), tol, scheme, p, stream=stream, check=False)
@@ -201,14 +228,15 @@ def tableau(kappa: float, tol: float = 1e-10, stream=None, s_values=(1.0, 16.0, 
     for s in s_values:
         for sg in sigma_values:
             grid[f"s={s:g},sigma={sg:g}"] = run("mixed_fp16", s=s, sigma=sg, sigma_lambda=sg if sg > 0 else 64.0)
-    corners = {}
-    for recalc in (0, 1):
-        for lam in (0, 1):
-            corners[f"recalc_gamma={recalc},rescale_x={lam}"] = run("mixed_fp16", recalc_gamma=recalc, rescale_x=lam)
-    out = {"lattice": list(dims), "kappa": kappa, "source": source, "grid": grid, "corners": corners,
-           "fp16_unrescaled_alg2": run("mixed_fp16_plain"),
-           "fp32_alg2_eps2_1e-4": run("mixed_fp32"),
-           "fp64": run("fp64")}
+    out = {"lattice": list(dims), "kappa": kappa, "source": source, "ftz": ftz, "grid": grid}
+    if extras:
+        corners = {}
+        for recalc in (0, 1):
+            for lam in (0, 1):
+                corners[f"recalc_gamma={recalc},rescale_x={lam}"] = run("mixed_fp16", recalc_gamma=recalc,
+                                                                        rescale_x=lam)
+        out.update({"corners": corners, "fp16_unrescaled_alg2": run("mixed_fp16_plain"),
+                    "fp32_alg2_eps2_1e-4": run("mixed_fp32"), "fp64": run("fp64")})
     lat.close()
     return out
 

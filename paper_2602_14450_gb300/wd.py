@@ -35,7 +35,7 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
            "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit", "wd_apply_batch",
-           "wd_set_rhs_per_thread"]
+           "wd_set_rhs_per_thread", "wd_fma_probe"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -113,12 +113,33 @@ def lib():
         L.wd_dd_hop_faces.argtypes = [vp, i, i, C.POINTER(vp), d, vp, vp]
         L.wd_vec_dot.argtypes = [vp, i, vp, vp, C.POINTER(d), vp]
         L.wd_vec_axpby.argtypes = [vp, i, C.POINTER(d), vp, C.POINTER(d), vp, vp]
+        L.wd_fma_probe.argtypes = [i, C.c_longlong, vp, vp, C.POINTER(d)]
         L.wd_status_string.argtypes = [i]
         L.wd_status_string.restype = C.c_char_p
         L.wd_last_error.argtypes = [vp]
         L.wd_last_error.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def fma_peak(bits, iters=1 << 14, stream=None):
+    """Measured FMA throughput of the FP64 (64), FP32 (32) or packed FP16 (16) pipe in
+    TFLOP/s: wd_fma_probe timed with CUDA events (one warm-up launch, then three)."""
+    import torch
+    sink = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    st = _stream(stream)
+    fl = C.c_double()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    rc = lib().wd_fma_probe(int(bits), int(iters), _ptr(sink), st, C.byref(fl))
+    if rc:
+        raise WDError(rc, "wd_fma_probe")
+    s = torch.cuda.current_stream() if stream is None else stream
+    ev[0].record(s)
+    for _ in range(3):
+        lib().wd_fma_probe(int(bits), int(iters), _ptr(sink), st, C.byref(fl))
+    ev[1].record(s)
+    ev[1].synchronize()
+    return 3 * fl.value / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e12
 
 
 class WDError(RuntimeError):
