@@ -424,7 +424,7 @@ namespace wd {
 // F = one even channel. One block row per (k, c) = (blockIdx.y, blockIdx.z).
 template <typename LT, int R>
 __global__ void __launch_bounds__(128) k_ptc_wgrad(Geom g, int mode, const uint4* G, const uint4* F, long long hvs,
-                                                   const uint4* links_e, const uint4* links_o, float* grad) {
+                                                   const uint4* links_e, const uint4* links_o, float* part) {
     const int k = blockIdx.y, c = blockIdx.z;
     float acc[32];
 #pragma unroll
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(128) k_ptc_wgrad(Geom g, int mode, const uint4
                     }
         }
     }
-    // block sum of the 32 accumulators, then one atomic add per value
+    // block sum of the 32 accumulators into this block's partial-sum slots (summed in block order later)
     __shared__ float sh[32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -474,8 +474,16 @@ __global__ void __launch_bounds__(128) k_ptc_wgrad(Geom g, int mode, const uint4
     if (threadIdx.x < 32) {
         float v = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
-        atomicAdd(grad + 2 * ((k * PTC_C + c) * 16) + threadIdx.x, v);
+        part[((size_t)(k * PTC_C + c) * gridDim.x + blockIdx.x) * 32 + threadIdx.x] = v;
     }
+}
+
+// grad[(k, c)][32] += sum over the nb blocks of k_ptc_wgrad's partial sums, in block order (deterministic).
+__global__ void k_ptc_wgrad_sum(int nb, const float* part, float* grad) {
+    const int kc = blockIdx.x;   // k * PTC_C + c
+    float v = 0.f;
+    for (int b = 0; b < nb; ++b) v += part[((size_t)kc * nb + b) * 32 + threadIdx.x];
+    grad[2 * (kc * 16) + threadIdx.x] += v;
 }
 
 }  // namespace wd
@@ -490,14 +498,23 @@ __global__ void k_f32_lincomb(long long n, float a, const float* x, float b, con
         z[i] = a * x[i] + (y ? b * y[i] : 0.f);
 }
 
-// out += sum x_i y_i (double accumulation, one atomic per block)
-__global__ void k_f32_dot(long long n, const float* x, const float* y, double* out) {
+// part[block] = this block's share of sum x_i y_i (double accumulation)
+__global__ void k_f32_dot(long long n, const float* x, const float* y, double* part) {
     double s = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         s += (double)x[i] * (double)y[i];
     double v[1] = {s};
     block_sum<1>(v);
-    if (threadIdx.x == 0) atomicAdd(out, v[0]);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+// *out = sum of nb partial sums in block order (deterministic)
+__global__ void k_sum_partials(int nb, const double* part, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[b];
+        *out = s;
+    }
 }
 
 // gamma5 of the Dirac representation: (g5 f)_s = -f_{s xor 2}
@@ -692,22 +709,30 @@ int ptc_grad(wd_handle* h, int n, const float* v, const float* y, double mu, dou
     float* t2 = (float*)workspace(h, "ptc.vt2", vb);
     float* gv = (float*)workspace(h, "ptc.vg", vb);
     double* dots = (double*)workspace(h, "ptc.dots", sizeof(double) * (4 * n + 4));
-    if (!H || !GH || !m || !e1 || !am || !t1 || !t2 || !gv || !dots) return fail(h, WD_ERR_CUDA, "out of device memory");
     const int blk = 256, gv1 = grid_for((int)std::min<long long>(nf, 1LL << 30), blk);
+    const dim3 wgrid(std::max(1, num_sms() / 8), 9, PTC_C);
+    // per-block partial sums of the dot products and of the weight gradients, summed in block order
+    double* dpart = (double*)workspace(h, "ptc.dpart", sizeof(double) * gv1);
+    float* wpart = (float*)workspace(h, "ptc.wpart", sizeof(float) * 32 * wgrid.x * 9 * PTC_C);
+    if (!H || !GH || !m || !e1 || !am || !t1 || !t2 || !gv || !dots || !dpart || !wpart)
+        return fail(h, WD_ERR_CUDA, "out of device memory");
+    auto dot = [&](const float* a, const float* b, double* out) {
+        k_f32_dot<<<gv1, blk, 0, s>>>(nf, a, b, dpart);
+        k_sum_partials<<<1, 32, 0, s>>>(gv1, dpart, out);
+    };
     WD_CUDA(h, cudaMemsetAsync(dots, 0, sizeof(double) * (4 * n + 4), s));
     WD_CUDA(h, cudaMemsetAsync(B.grad, 0, sizeof(float) * PTC_FLOATS, s));
     // input norms first: the gradient coefficients need them
     for (int i = 0; i < n; ++i) {
         const float* vi = v + i * nf;
         const float* yi = y + i * nf;
-        k_f32_dot<<<gv1, blk, 0, s>>>(nf, vi, vi, dots + 4 * i);
-        k_f32_dot<<<gv1, blk, 0, s>>>(nf, yi, yi, dots + 4 * i + 1);
+        dot(vi, vi, dots + 4 * i);
+        dot(yi, yi, dots + 4 * i + 1);
     }
     std::vector<double> hd(4 * n + 4);
     WD_CUDA(h, cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (4 * n + 4), cudaMemcpyDeviceToHost, s));
     WD_CUDA(h, cudaStreamSynchronize(s));
     const int gx = grid_for(g.Vh, 128);
-    const dim3 wgrid(std::max(1, num_sms() / 8), 9, PTC_C);
     k_ptc_adjoint_weights<<<1, 256, 0, s>>>(B.weff + 2 * PTC_LAYER, B.wadj);
     for (int i = 0; i < n; ++i) {
         const float* vi = v + i * nf;
@@ -719,19 +744,21 @@ int ptc_grad(wd_handle* h, int n, const float* v, const float* y, double mu, dou
         k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, 1.f, m, -1.f, yi, e1);
         WD_CUDA(h, apply_A_f32(h, (const uint4*)m, (uint4*)am, (uint4*)t1, le, lo, s));
         k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, 1.f, am, -1.f, vi, am);
-        k_f32_dot<<<gv1, blk, 0, s>>>(nf, e1, e1, dots + 4 * i + 2);
-        k_f32_dot<<<gv1, blk, 0, s>>>(nf, am, am, dots + 4 * i + 3);
+        dot(e1, e1, dots + 4 * i + 2);
+        dot(am, am, dots + 4 * i + 3);
         k_gamma5_f32<<<gx, 128, 0, s>>>(g.Vh, (const uint4*)am, (uint4*)t2);
         WD_CUDA(h, apply_A_f32(h, (const uint4*)t2, (uint4*)gv, (uint4*)t1, le, lo, s));
         k_gamma5_f32<<<gx, 128, 0, s>>>(g.Vh, (const uint4*)gv, (uint4*)t2);
         // g = 2 e1 / |y|^2 + 2 mu A^+ e2 / |v|^2  (= 2 dL/dconj(m))
         k_f32_lincomb<<<gv1, blk, 0, s>>>(nf, (float)(2.0 / ny), e1, (float)(2.0 * mu / nv), t2, gv);
         // layer 2: dW2 += sum g (x) conj(T_k H_c) ; g_H = adjoint network of layer 2 applied to g
-        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 0, (const uint4*)gv, H, hvs, le, lo, B.grad + 2 * PTC_LAYER);
+        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 0, (const uint4*)gv, H, hvs, le, lo, wpart);
+        k_ptc_wgrad_sum<<<9 * PTC_C, 32, 0, s>>>(wgrid.x, wpart, B.grad + 2 * PTC_LAYER);
         k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), 128, 0, s>>>(g, (const uint4*)gv, nullptr, GH, hvs,
                                                                                le, lo, B.wadj, nullptr);
         // layer 1: dW1 += sum g_H,c (x) conj(T_k v)
-        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 1, GH, (const uint4*)vi, hvs, le, lo, B.grad);
+        k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 1, GH, (const uint4*)vi, hvs, le, lo, wpart);
+        k_ptc_wgrad_sum<<<9 * PTC_C, 32, 0, s>>>(wgrid.x, wpart, B.grad);
         WD_CUDA(h, cudaGetLastError());
     }
     WD_CUDA(h, cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (4 * n + 4), cudaMemcpyDeviceToHost, s));

@@ -157,3 +157,20 @@ def test_trained_network_reduces_matvecs():
         counts[scheme] = st.inner_matvecs
     print(f"\nFP16 matvecs to 1e-10, 8^3 x 16: plain {counts['mixed_fp16']}, learned M {counts['mixed_fp16_learned']}")
     assert counts["mixed_fp16_learned"] < 0.9 * counts["mixed_fp16"], counts
+
+
+def test_training_is_reproducible():
+    """Every sum of the training step (the loss's dot products, the weight
+    gradients over sites and blocks) is taken in a fixed order, so two runs
+    from the same weights on the same samples give the same losses and the
+    same weights, bit for bit."""
+    dims = (8, 8, 8, 8)
+    lat = lattice(synth.gauge_smeared(dims, seed=71), 0.12, dims)
+    v, y = learned.make_samples(lat, 4, seed=700)
+    runs = []
+    for _ in range(2):
+        lat.precond_set(learned.initial_weights(5))
+        losses = learned.train(lat, v, y, steps=6, lr=3e-3, mu=1.0, batch=2)
+        runs.append((losses, lat.precond_get()))
+    assert runs[0][0] == runs[1][0]
+    assert torch.equal(runs[0][1], runs[1][1])
