@@ -21,39 +21,89 @@ __device__ __forceinline__ void cscale_add(C& or_, C& oi, C ar, C ai, C vr, C vi
 // Per right-hand-side loop over the sites of a batched launch.
 #define RHS_LOOP(h, n) for (int h = sl.b * blockDim.x + threadIdx.x; h < (n); h += sl.nb * blockDim.x)
 
+// The streaming kernels below work unit by unit (a unit = 16 bytes: 8 halves,
+// 4 floats or 2 doubles of one site) and issue every load of a chunk of units
+// -- for FP16/BF16 storage the whole site, for two sites per thread -- before
+// the first store, so that a thread keeps all its reads in flight at once
+// (the vectors may alias as far as the compiler knows, so a load written after
+// a store would wait for it). The arithmetic per element and the order of
+// every per-thread sum are those of a site-by-site loop.
+template <typename T> struct Stream {
+    static constexpr int N = Unit<T>::N;                     // reals per unit
+    static constexpr int SU = 24 / N;                        // units per site
+    static constexpr int CH = SU < 3 ? SU : 3;               // units per chunk
+    static constexpr int SITES = sizeof(T) == 2 ? 2 : 1;     // sites per thread and step
+};
+
+// Round the N values of one unit to storage, write it (flushing stored
+// subnormals with ftz) and replace the values by the stored ones.
+template <typename T>
+__device__ __forceinline__ void store_unit(uint4* v, size_t off, typename Unit<T>::C (&c)[Unit<T>::N], bool ftz) {
+    uint4 w = Unit<T>::put(c);
+    if (ftz) w = Unit<T>::flush(w);
+    v[off] = w;
+#pragma unroll
+    for (int i = 0; i < Unit<T>::N; ++i) c[i] = Unit<T>::get(w, i);
+}
+
+// Per right-hand-side loop over groups of S sites of a batched launch: sites h, h + step, ... h + (S-1) step.
+#define RHS_LOOP_S(h, n, S) for (int h = sl.b * blockDim.x + threadIdx.x; h < (n); h += (S) * sl.nb * blockDim.x)
+
 // p := r (first iteration) or cP p - cV v + r
 template <typename T>
 __global__ void __launch_bounds__(256) k_pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v,
                                                  const uint4* r, const SolverState* sts) {
     pdl_begin();
     typedef typename Unit<T>::C C;
+    typedef Stream<T> ST;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
     if (guarded(st, GUARD_INNER)) return;
     const long long ro = sl.rhs * vs;
     p += ro; v += ro; r += ro;
-    const bool first = st->first;
+    const bool first = st->first, ftz = st->ftz;
     const C pr = (C)st->cP[0], pi = (C)st->cP[1], vr = (C)st->cV[0], vi = (C)st->cV[1];
-    RHS_LOOP(h, n) {
-        C rr[24], o[24];
-        load_spinor<T>(r, n, h, rr);
-        if (first) {
+    const int step = sl.nb * blockDim.x;
+    RHS_LOOP_S(h0, n, ST::SITES) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) o[i] = rr[i];
-        } else {
-            C pp[24], vv[24];
-            load_spinor<T>(p, n, h, pp);
-            load_spinor<T>(v, n, h, vv);
+        for (int u0 = 0; u0 < ST::SU; u0 += ST::CH) {
+            uint4 ur[ST::SITES][ST::CH], up[ST::SITES][ST::CH], uv[ST::SITES][ST::CH];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                C a = rr[2 * i], b = rr[2 * i + 1];
-                cscale_add(a, b, pr, pi, pp[2 * i], pp[2 * i + 1]);
-                cscale_add(a, b, -vr, -vi, vv[2 * i], vv[2 * i + 1]);
-                o[2 * i] = a;
-                o[2 * i + 1] = b;
+            for (int q = 0; q < ST::SITES; ++q) {
+                const int h = h0 + q * step;
+                if (h >= n) continue;
+#pragma unroll
+                for (int c = 0; c < ST::CH; ++c) {
+                    const size_t off = (size_t)(u0 + c) * n + h;
+                    ur[q][c] = __ldg(r + off);
+                    if (!first) {
+                        up[q][c] = __ldg(p + off);
+                        uv[q][c] = __ldg(v + off);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < ST::SITES; ++q) {
+                const int h = h0 + q * step;
+                if (h >= n) continue;
+#pragma unroll
+                for (int c = 0; c < ST::CH; ++c) {
+                    C o[ST::N];
+#pragma unroll
+                    for (int i = 0; i < ST::N / 2; ++i) {
+                        C a = Unit<T>::get(ur[q][c], 2 * i), b = Unit<T>::get(ur[q][c], 2 * i + 1);
+                        if (!first) {
+                            cscale_add(a, b, pr, pi, Unit<T>::get(up[q][c], 2 * i), Unit<T>::get(up[q][c], 2 * i + 1));
+                            cscale_add(a, b, -vr, -vi, Unit<T>::get(uv[q][c], 2 * i),
+                                       Unit<T>::get(uv[q][c], 2 * i + 1));
+                        }
+                        o[2 * i] = a;
+                        o[2 * i + 1] = b;
+                    }
+                    store_unit<T>(p, (size_t)(u0 + c) * n + h, o, ftz);
+                }
             }
         }
-        store_spinor<T>(p, n, h, o, st->ftz);
     }
 }
 
@@ -63,19 +113,47 @@ __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, 
                                                  const SolverState* sts) {
     pdl_begin();
     typedef typename Unit<T>::C C;
+    typedef Stream<T> ST;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
     if (guarded(st, GUARD_INNER)) return;
     const long long o = sl.rhs * vs;
     r += o; v += o;
+    const bool ftz = st->ftz;
     const C ar = (C)-st->alpha[0], ai = (C)-st->alpha[1];
-    RHS_LOOP(h, n) {
-        C rr[24], vv[24];
-        load_spinor<T>(r, n, h, rr);
-        load_spinor<T>(v, n, h, vv);
+    const int step = sl.nb * blockDim.x;
+    RHS_LOOP_S(h0, n, ST::SITES) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], ar, ai, vv[2 * i], vv[2 * i + 1]);
-        store_spinor<T>(r, n, h, rr, st->ftz);
+        for (int u0 = 0; u0 < ST::SU; u0 += ST::CH) {
+            uint4 ur[ST::SITES][ST::CH], uv[ST::SITES][ST::CH];
+#pragma unroll
+            for (int q = 0; q < ST::SITES; ++q) {
+                const int h = h0 + q * step;
+                if (h >= n) continue;
+#pragma unroll
+                for (int c = 0; c < ST::CH; ++c) {
+                    const size_t off = (size_t)(u0 + c) * n + h;
+                    ur[q][c] = __ldg(r + off);
+                    uv[q][c] = __ldg(v + off);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < ST::SITES; ++q) {
+                const int h = h0 + q * step;
+                if (h >= n) continue;
+#pragma unroll
+                for (int c = 0; c < ST::CH; ++c) {
+                    C rr[ST::N];
+#pragma unroll
+                    for (int i = 0; i < ST::N; ++i) rr[i] = Unit<T>::get(ur[q][c], i);
+#pragma unroll
+                    for (int i = 0; i < ST::N / 2; ++i)
+                        cscale_add(rr[2 * i], rr[2 * i + 1], ar, ai, Unit<T>::get(uv[q][c], 2 * i),
+                                   Unit<T>::get(uv[q][c], 2 * i + 1));
+                    store_unit<T>(r, (size_t)(u0 + c) * n + h, rr, ftz);
+                }
+            }
+        }
     }
 }
 
@@ -85,12 +163,14 @@ __global__ void __launch_bounds__(256) k_supdate(int n, int nrhs, long long vs, 
 // sums: XR_PLAIN  |r|^2, |x|^2, (r*, r)
 //       XR_NORMS  |r|^2, |x|^2            (a separate k_scale pass follows)
 //       XR_FUSED  |r|^2 (before scaling), |r_stored|^2, (r*, r_stored)
+// One site per thread and step: six vectors of a site are in flight at once.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4* x, uint4* r, const uint4* p,
                                             const uint4* t, const uint4* rstar, const uint4* xr_src,
                                             const uint4* xp_src, SolverState* sts, RedCtx rc) {
     pdl_begin();
     typedef typename Unit<T>::C C;
+    typedef Stream<T> ST;
     constexpr bool WITH_RS = MODE != XR_NORMS;
     const Slice sl = slice_of(nrhs);
     const SolverState* st = sts + sl.rhs;
@@ -100,52 +180,71 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
     // x-update sources: r and p, or M r and M p with a right preconditioner
     const uint4* xsr = xr_src ? xr_src + o : r;
     const uint4* xsp = xp_src ? xp_src + o : p;
-    const bool first = st->first;
+    const bool first = st->first, ftz = st->ftz, pre = xr_src != nullptr;
     const C xr_r = (C)st->cXr[0], xr_i = (C)st->cXr[1], xp_r = (C)st->cXp[0], xp_i = (C)st->cXp[1];
     const C om_r = (C)-st->omega[0], om_i = (C)-st->omega[1];
     const C gs = MODE == XR_FUSED ? (C)st->gam_tmp : (C)1;
     C s_r2 = 0, s_x2 = 0, s_re = 0, s_im = 0;
     RHS_LOOP(h, n) {
-        C rr[24], pp[24], xx[24], tt[24];
-        load_spinor<T>(xsr, n, h, rr);
-        load_spinor<T>(xsp, n, h, pp);
-        if (first) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) xx[i] = 0;
-        } else {
-            load_spinor<T>(x, n, h, xx);
-        }
+        for (int u0 = 0; u0 < ST::SU; u0 += ST::CH) {
+            uint4 ur[ST::CH], up[ST::CH], ux[ST::CH], ut[ST::CH], urs[ST::CH], urr[ST::CH];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            cscale_add(xx[2 * i], xx[2 * i + 1], xr_r, xr_i, rr[2 * i], rr[2 * i + 1]);
-            cscale_add(xx[2 * i], xx[2 * i + 1], xp_r, xp_i, pp[2 * i], pp[2 * i + 1]);
-        }
-        store_spinor<T>(x, n, h, xx, st->ftz);
-        if (xr_src) load_spinor<T>(r, n, h, rr);
-        load_spinor<T>(t, n, h, tt);
+            for (int c = 0; c < ST::CH; ++c) {
+                const size_t off = (size_t)(u0 + c) * n + h;
+                ur[c] = __ldg(xsr + off);
+                up[c] = __ldg(xsp + off);
+                if (!first) ux[c] = __ldg(x + off);
+                ut[c] = __ldg(t + off);
+                if (pre) urr[c] = __ldg(r + off);
+                if constexpr (WITH_RS) urs[c] = __ldg(rstar + off);
+            }
 #pragma unroll
-        for (int i = 0; i < 12; ++i) cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, tt[2 * i], tt[2 * i + 1]);
+            for (int c = 0; c < ST::CH; ++c) {
+                const size_t off = (size_t)(u0 + c) * n + h;
+                C xx[ST::N], rr[ST::N];
 #pragma unroll
-        for (int i = 0; i < 24; ++i) s_r2 += rr[i] * rr[i];
-        if constexpr (MODE == XR_FUSED) {
+                for (int i = 0; i < ST::N; ++i) {
+                    xx[i] = first ? (C)0 : Unit<T>::get(ux[c], i);
+                    rr[i] = Unit<T>::get(ur[c], i);
+                }
 #pragma unroll
-            for (int i = 0; i < 24; ++i) rr[i] *= gs;
-        }
-        store_spinor<T>(r, n, h, rr, st->ftz);
-        if constexpr (MODE == XR_FUSED) {
+                for (int i = 0; i < ST::N / 2; ++i) {
+                    cscale_add(xx[2 * i], xx[2 * i + 1], xr_r, xr_i, rr[2 * i], rr[2 * i + 1]);
+                    cscale_add(xx[2 * i], xx[2 * i + 1], xp_r, xp_i, Unit<T>::get(up[c], 2 * i),
+                               Unit<T>::get(up[c], 2 * i + 1));
+                }
+                store_unit<T>(x, off, xx, ftz);
+                if (pre) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) s_x2 += rr[i] * rr[i];      // |r_stored|^2
-        } else {
+                    for (int i = 0; i < ST::N; ++i) rr[i] = Unit<T>::get(urr[c], i);
+                }
 #pragma unroll
-            for (int i = 0; i < 24; ++i) s_x2 += xx[i] * xx[i];
-        }
-        if constexpr (WITH_RS) {
-            C rs[24];
-            load_spinor<T>(rstar, n, h, rs);
+                for (int i = 0; i < ST::N / 2; ++i)
+                    cscale_add(rr[2 * i], rr[2 * i + 1], om_r, om_i, Unit<T>::get(ut[c], 2 * i),
+                               Unit<T>::get(ut[c], 2 * i + 1));
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                s_re += rs[2 * i] * rr[2 * i] + rs[2 * i + 1] * rr[2 * i + 1];
-                s_im += rs[2 * i] * rr[2 * i + 1] - rs[2 * i + 1] * rr[2 * i];
+                for (int i = 0; i < ST::N; ++i) s_r2 += rr[i] * rr[i];
+                if constexpr (MODE == XR_FUSED) {
+#pragma unroll
+                    for (int i = 0; i < ST::N; ++i) rr[i] *= gs;
+                }
+                store_unit<T>(r, off, rr, ftz);
+                if constexpr (MODE == XR_FUSED) {
+#pragma unroll
+                    for (int i = 0; i < ST::N; ++i) s_x2 += rr[i] * rr[i];      // |r_stored|^2
+                } else {
+#pragma unroll
+                    for (int i = 0; i < ST::N; ++i) s_x2 += xx[i] * xx[i];
+                }
+                if constexpr (WITH_RS) {
+#pragma unroll
+                    for (int i = 0; i < ST::N / 2; ++i) {
+                        const C rsr = Unit<T>::get(urs[c], 2 * i), rsi = Unit<T>::get(urs[c], 2 * i + 1);
+                        s_re += rsr * rr[2 * i] + rsi * rr[2 * i + 1];
+                        s_im += rsr * rr[2 * i + 1] - rsi * rr[2 * i];
+                    }
+                }
             }
         }
     }

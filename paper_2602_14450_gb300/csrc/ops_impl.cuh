@@ -279,14 +279,14 @@ cudaError_t Ops<T>::mat_from64(int n, const uint4* src64, uint4* dst, cudaStream
 template <typename T>
 cudaError_t Ops<T>::pupdate(int n, int nrhs, long long vs, uint4* p, const uint4* v, const uint4* r,
                             const SolverState* st, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_pupdate<T>, stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, p, v, r, st); if (le_ != cudaSuccess) return le_; }
+    { const cudaError_t le_ = launch_k(k_pupdate<T>, stream_blocks((n + Stream<T>::SITES - 1) / Stream<T>::SITES, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, p, v, r, st); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Ops<T>::supdate(int n, int nrhs, long long vs, uint4* r, const uint4* v, const SolverState* st,
                             cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_supdate<T>, stream_blocks(n, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, r, v, st); if (le_ != cudaSuccess) return le_; }
+    { const cudaError_t le_ = launch_k(k_supdate<T>, stream_blocks((n + Stream<T>::SITES - 1) / Stream<T>::SITES, VEC_BLOCK) * nrhs, VEC_BLOCK, 0, s, n, nrhs, vs, r, v, st); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 
