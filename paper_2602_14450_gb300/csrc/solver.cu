@@ -225,16 +225,37 @@ static cudaError_t enqueue_iteration(const Sys& S, int prec, int recon, int xr_m
     });
 }
 
-// Capture `iters` iterations of every system plus the activity flag.
+// Capture `iters` iterations of every system plus the activity flag. Systems
+// of different handles are independent (their own vectors, scalar states,
+// partial sums and tickets), so each is captured on its own handle's stream,
+// forked from and joined back into the first: the graph runs the lattices'
+// iterations side by side, and the kernels of a small lattice overlap those of
+// a large one instead of queueing behind them.
 static int capture_inner(std::vector<Sys>& sys, int prec, int recon, int xr_mode, bool learned, int iters,
                          cudaGraphExec_t* out) {
     wd_handle* h0 = sys[0].h;
+    bool branches = sys.size() > 1;
+    for (size_t i = 0; i < sys.size() && branches; ++i)
+        for (size_t j = 0; j < i; ++j)
+            if (sys[i].h == sys[j].h) branches = false;   // one handle twice: its stream cannot fork from itself
     cudaGraph_t graph = nullptr;
     WD_CUDA(h0, cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < iters && e == cudaSuccess; ++i)
-        for (auto& S : sys)
-            if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, xr_mode, learned, h0->cap);
+    if (branches) {
+        e = cudaEventRecord(h0->ev[1], h0->cap);                                   // fork
+        for (size_t i = 1; i < sys.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(sys[i].h->cap, h0->ev[1], 0);
+        for (size_t i = 0; i < sys.size() && e == cudaSuccess; ++i)
+            for (int it = 0; it < iters && e == cudaSuccess; ++it)
+                e = enqueue_iteration(sys[i], prec, recon, xr_mode, learned, sys[i].h->cap);
+        for (size_t i = 1; i < sys.size() && e == cudaSuccess; ++i) {              // join
+            e = cudaEventRecord(sys[i].h->ev[0], sys[i].h->cap);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h0->cap, sys[i].h->ev[0], 0);
+        }
+    } else {
+        for (int i = 0; i < iters && e == cudaSuccess; ++i)
+            for (auto& S : sys)
+                if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, xr_mode, learned, h0->cap);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h0->dflag, 0, sizeof(int), h0->cap);
     for (auto& S : sys) {
         if (e != cudaSuccess) break;
