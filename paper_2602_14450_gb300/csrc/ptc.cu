@@ -593,13 +593,55 @@ static uint4* ptc_hidden(wd_handle* h, int prec, const char* name) {
 
 // M in = out: FP32 path (FP32 hidden, FP32 18-real links) or FP16 path
 // (BF16 hidden, FP16 12-real links), weights from `w` (device, flat layout).
+int* ptc_err(wd_handle* h);
+
+// Whether M (its first pass, and in training the fan-out layers) mixes channels
+// on the tensor cores (environment WD_PTC_TC=0 selects the FP32-core kernels).
+static bool ptc_tensor_cores() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("WD_PTC_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Training fan-out (FP32 input on the even sites, FP32 18-real links) into the
+// 12 hidden channels of H on both parities: the even sites (hop 0 only) on the
+// FP32 cores, the odd sites (the eight transports) on the tensor cores.
+static cudaError_t ptc_fanout_f32(wd_handle* h, const uint4* in_e, uint4* H, long long hvs, const uint4* le,
+                                  const uint4* lo, const float* w, cudaStream_t s, int* err) {
+    const Geom& g = h->g;
+    const int gx = grid_for(g.Vh, 128);
+    if (!ptc_tensor_cores()) {
+        k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), 128, 0, s>>>(g, in_e, nullptr, H, hvs, le, lo, w,
+                                                                               nullptr);
+        return cudaGetLastError();
+    }
+    k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 1), 128, 0, s>>>(g, in_e, nullptr, H, hvs, le, lo, w,
+                                                                           nullptr);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_ptc_fanout_odd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tcf::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = ((long long)g.Vh + tc::TILE_M - 1) / tc::TILE_M;
+    const long long tcap = (long long)num_sms() * 3;
+    const int gt = (int)(tiles < tcap ? tiles : tcap);
+    k_ptc_fanout_odd_tc<<<gt, 128, tcf::SMEM_BYTES, s>>>(g, in_e, H, hvs, lo, w, err, h->wait_rounds);
+    return cudaGetLastError();
+}
+
 cudaError_t ptc_apply_raw(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* H, const float* w,
                           const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard) {
     const Geom& g = h->g;
     const int blk = 128, gx = grid_for(g.Vh, blk);
     if (prec == WD_FP32) {
         const long long hvs = (long long)spinor_units(WD_FP32) * g.Vh;
-        k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), blk, 0, s>>>(g, in_e, nullptr, H, hvs, le, lo, w, guard);
+        cudaError_t e = ptc_fanout_f32(h, in_e, H, hvs, le, lo, w, s, ptc_err(h));
+        if (e != cudaSuccess) return e;
         k_ptc_fanin<float, float, float, 18><<<gx, blk, 0, s>>>(g, H, hvs, out_e, le, w + 2 * PTC_LAYER, guard);
     } else {
         const long long hvs = (long long)spinor_units(WD_BF16) * g.Vh;
@@ -620,17 +662,6 @@ static uint4* ptc_phi(wd_handle* h, int prec) {
                            : (uint4*)workspace(h, "ptc.phi16", vec_bytes(h, WD_BF16) * 8);
 }
 
-// out = M in through the collapsed form: FP32 path (FP32 fields, FP32 18-real
-// links) or FP16 path (FP16 in/out, BF16 phi, FP16 12-real links).
-// Whether the FP16 path mixes on the tensor cores (environment WD_PTC_TC=0 selects the FP32-core pass).
-static bool ptc_tensor_cores() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = std::getenv("WD_PTC_TC");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
 
 cudaError_t ptc_apply_m(wd_handle* h, int prec, const uint4* in_e, uint4* out_e, uint4* PHI, const float2* V,
                         const uint4* le, const uint4* lo, cudaStream_t s, const SolverState* guard, int* err) {
@@ -720,6 +751,9 @@ int ptc_grad(wd_handle* h, int n, const float* v, const float* y, double mu, dou
         k_f32_dot<<<gv1, blk, 0, s>>>(nf, a, b, dpart);
         k_sum_partials<<<1, 32, 0, s>>>(gv1, dpart, out);
     };
+    int* err = ptc_err(h);
+    if (!err) return fail(h, WD_ERR_CUDA, "out of device memory");
+    WD_CUDA(h, cudaMemsetAsync(err, 0, sizeof(int), s));
     WD_CUDA(h, cudaMemsetAsync(dots, 0, sizeof(double) * (4 * n + 4), s));
     WD_CUDA(h, cudaMemsetAsync(B.grad, 0, sizeof(float) * PTC_FLOATS, s));
     // input norms first: the gradient coefficients need them
@@ -754,15 +788,17 @@ int ptc_grad(wd_handle* h, int n, const float* v, const float* y, double mu, dou
         // layer 2: dW2 += sum g (x) conj(T_k H_c) ; g_H = adjoint network of layer 2 applied to g
         k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 0, (const uint4*)gv, H, hvs, le, lo, wpart);
         k_ptc_wgrad_sum<<<9 * PTC_C, 32, 0, s>>>(wgrid.x, wpart, B.grad + 2 * PTC_LAYER);
-        k_ptc_fanout<float, float, float, 18><<<dim3(gx, PTC_C, 2), 128, 0, s>>>(g, (const uint4*)gv, nullptr, GH, hvs,
-                                                                               le, lo, B.wadj, nullptr);
+        WD_CUDA(h, ptc_fanout_f32(h, (const uint4*)gv, GH, hvs, le, lo, B.wadj, s, err));
         // layer 1: dW1 += sum g_H,c (x) conj(T_k v)
         k_ptc_wgrad<float, 18><<<wgrid, 128, 0, s>>>(g, 1, GH, (const uint4*)vi, hvs, le, lo, wpart);
         k_ptc_wgrad_sum<<<9 * PTC_C, 32, 0, s>>>(wgrid.x, wpart, B.grad);
         WD_CUDA(h, cudaGetLastError());
     }
     WD_CUDA(h, cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (4 * n + 4), cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    WD_CUDA(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     WD_CUDA(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, WD_ERR_TIMEOUT, "wd_precond_grad: a bounded tensor-core wait gave up");
     double L = 0.0;
     for (int i = 0; i < n; ++i) L += hd[4 * i + 2] / hd[4 * i + 1] + mu * hd[4 * i + 3] / hd[4 * i];
     if (loss) *loss = L;

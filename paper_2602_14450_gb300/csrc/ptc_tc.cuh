@@ -60,11 +60,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                            ((uint32_t)(TILE_M >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+// The same descriptor for another N (a multiple of 16 up to 256) at M = 128.
+constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TILE_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                         uint32_t idesc = IDESC) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -263,6 +269,152 @@ __global__ void __launch_bounds__(128, 3) k_ptc_s1_tc(Geom g, const uint4* in_e,
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// Training: the odd-site half of a fan-out layer, H_c(y) = sum_{d,t} W[1+d][c]_{st}
+// (T_{1+d} in)(y)_{t,a} for the 12 channels c, with the input on the even
+// sites only (the forward layer 1 on v, and the adjoint of layer 2 on the loss
+// gradient): the same contraction as the first pass of M with the channel
+// mixing as B, per (site, colour) row K = 64 (d, t, re/im) against N = 96
+// (c, s, re/im):
+//   B = [[Re W, -Im W], [Im W, Re W]],  n = 8 c + 2 s + c',  k = 8 d + 2 t + c.
+// FP32 input and 18-real FP32 links (the training precision), transports in
+// FP32 rounded to BF16 operands, FP32 accumulation in 128 TMEM columns,
+// written to H in FP32 (layout [c][parity][units][Vh], parity 1 here). The
+// waits are bounded as in k_ptc_s1_tc.
+namespace tcf {
+constexpr int N = 96;
+constexpr int B_BYTES = N * tc::K * 2;                                 // 12 KB
+constexpr int SMEM_BYTES = 3 * tc::A_TILE_BYTES + B_BYTES + 64;
+constexpr int TMEM_COLS = 128;
+constexpr uint32_t IDESC = tc::idesc_bf16(N);
+}  // namespace tcf
+
+__global__ void __launch_bounds__(128) k_ptc_fanout_odd_tc(Geom g, const uint4* in_e, uint4* H, long long hvs,
+                                                           const uint4* links_o, const float* w, int* err,
+                                                           unsigned wait_rounds) {
+    using namespace tc;
+    const unsigned limit = wait_rounds ? wait_rounds - 1 : WAIT_LIMIT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* A = smem;                              // 3 colour tiles
+    unsigned char* Bt = smem + 3 * A_TILE_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Bt + tcf::B_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(Bt + tcf::B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    for (int i = tid; i < tcf::N * K; i += blockDim.x) {
+        const int n = i / K, k = i % K;
+        const int c = n >> 3, s = (n >> 1) & 3, co = n & 1;
+        const int d = k >> 3, t = (k >> 1) & 3, ci = k & 1;
+        const float* wp = w + 2 * (((1 + d) * PTC_C + c) * 16 + 4 * s + t);
+        const float val = co == 0 ? (ci == 0 ? wp[0] : -wp[1]) : (ci == 0 ? wp[1] : wp[0]);
+        *reinterpret_cast<__nv_bfloat16*>(Bt + kmajor_offset(n, k)) = __float2bfloat16_rn(val);
+    }
+    if (tid == 0) {
+        bar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
+                     "r"(tcf::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const uint32_t a_base = smem_addr(A), b_base = smem_addr(Bt);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    const int ntiles = (g.Vh + TILE_M - 1) / TILE_M;
+    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const int h = tile * TILE_M + tid;
+        const bool ok = h < g.Vh;
+        const Coord co = ok ? coord_of(g, 1, h) : Coord{};
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            float t[24];
+            if (ok) {
+                bool wrap;
+                const int hn = neighbour(g, h, co, d, &wrap);
+                float f[24], m[18];
+                load_spinor<float>(in_e, g.Vh, hn, f);
+                load_link<float, 18>(links_o, g.Vh, h, d, m);
+                colour_mul(m, f, t);
+                if (wrap && g.bc[d >> 1] < 0) {
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) t[i] = -t[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 24; ++i) t[i] = 0.f;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {   // k = 8 d + 2 t + c: spins 0..3 of colour a, (re, im)
+                uint4 u;
+                u.x = pack_bf16(t[2 * (0 + a)], t[2 * (0 + a) + 1]);
+                u.y = pack_bf16(t[2 * (3 + a)], t[2 * (3 + a) + 1]);
+                u.z = pack_bf16(t[2 * (6 + a)], t[2 * (6 + a) + 1]);
+                u.w = pack_bf16(t[2 * (9 + a)], t[2 * (9 + a) + 1]);
+                *reinterpret_cast<uint4*>(A + a * A_TILE_BYTES + kmajor_offset(tid, 8 * d)) = u;
+            }
+        }
+        fence_proxy_async();
+        fence_before();
+        __syncthreads();
+        fence_after();
+
+#pragma unroll 1
+        for (int a = 0; a < 3; ++a) {
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < K / 16; ++j) {
+                    const uint64_t ad = smem_desc(a_base + a * A_TILE_BYTES + 256 * j, 128, 1024);
+                    const uint64_t bd = smem_desc(b_base + 256 * j, 128, 1024);
+                    tc::mma_bf16(tmem, ad, bd, j > 0 ? 1u : 0u, tcf::IDESC);
+                }
+                mma_commit(bar);
+            }
+            const bool landed = bar_wait(bar, phase, limit);
+            failed = __syncthreads_or(!landed);
+            if (failed) {
+                if (tid == 0 && err) atomicExch(err, 1);
+                break;
+            }
+            phase ^= 1;
+            fence_after();
+            // every lane takes part in the aligned TMEM loads; rows past the end are not stored
+#pragma unroll 1
+            for (int c = 0; c < PTC_C; ++c) {
+                float v[8];
+                tmem_ld8(tmem + lane_base + 8 * c, v);
+                tmem_ld_wait();
+                if (ok) {
+                    float* out = reinterpret_cast<float*>(H + (size_t)(2 * c + 1) * hvs);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {   // (re, im) of spin s, colour a: reals 2 (3 s + a), + 1
+                        const int i = 2 * (3 * s + a);
+                        *reinterpret_cast<float2*>(out + ((size_t)(i >> 2) * g.Vh + h) * 4 + (i & 3)) =
+                            make_float2(v[2 * s], v[2 * s + 1]);
+                    }
+                }
+            }
+            fence_before();
+            __syncthreads();
+            fence_after();
+        }
+    }
+    if (failed && tid == 0) bar_wait(bar, phase);   // default bound: let an MMA still in flight finish
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcf::TMEM_COLS)
+                     : "memory");
 }
 
 }  // namespace wd

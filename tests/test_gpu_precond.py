@@ -67,6 +67,28 @@ def test_identity_weights(setup):
 
 
 def test_gradients_match_oracle(setup):
+    """Loss and weight gradients of wd_precond_grad against the oracle's
+    autograd (itself pinned by finite differences). The fan-out layers (the
+    forward layer 1 and the adjoint of layer 2) mix channels on the tensor cores
+    with BF16 operands: loss within 1e-4, gradients within 1e-3 (measured
+    2e-5 and 4e-4). With WD_PTC_TC=0 (FP32 cores, a child process) within 1e-5
+    and 1e-4."""
+    import os
+    check_gradients(setup, 1e-4, 1e-3)
+    if os.environ.get("WD_PTC_TC") != "0":
+        import subprocess
+        import sys
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        code = ("import sys; sys.path.insert(0, %r); from tests import test_gpu_precond as t; "
+                "from oracle import ptc; from paper_2602_14450_gb300 import synth; "
+                "u = synth.gauge_random(t.DIMS, 0.5, seed=61); "
+                "t.check_gradients((u, t.lattice(u, t.KAPPA, t.DIMS)), 1e-5, 1e-4); print('fp32 cores ok')" % root)
+        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, WD_PTC_TC="0"), capture_output=True,
+                           text=True, timeout=300, cwd=root)
+        assert r.returncode == 0 and "fp32 cores ok" in r.stdout, r.stdout + r.stderr
+
+
+def check_gradients(setup, loss_tol, grad_tol):
     u, lat = setup
     flat, (w1, w2) = bf16_weights(seed=8)
     lat.precond_set(flat)
@@ -80,10 +102,10 @@ def test_gradients_match_oracle(setup):
     vs32 = [unpacked_even(lat, "fp32", packed_even(lat, "fp32", f), DIMS) for f in vs]
     ys32 = [unpacked_even(lat, "fp32", packed_even(lat, "fp32", f), DIMS) for f in ys]
     L, g1, g2 = ptc.grads(u, w1, w2, vs32, ys32, KAPPA, mu, BC)
-    assert abs(loss - L) <= 1e-5 * L
+    assert abs(loss - L) <= loss_tol * L
     want = ptc.to_flat(g1, g2)
     got = g.cpu().double()
-    assert (torch.linalg.vector_norm(got - want) / torch.linalg.vector_norm(want)).item() <= 1e-4
+    assert (torch.linalg.vector_norm(got - want) / torch.linalg.vector_norm(want)).item() <= grad_tol
 
 
 def test_training_lowers_the_loss_and_preconditioned_solve_converges(setup):
