@@ -236,9 +236,10 @@ def main():
     prm = wd.default_params("mixed_fp16")
     stream = torch.cuda.current_stream()
     # the library's autotuner picks the hop kernel variant and block size for the inner and outer precisions
+    # (with the headline's stencil arithmetic set, so that the FP16-arithmetic hop's shape is tuned too)
+    lat.set_arith(args.arith)
     tuning = {} if args.no_tune else {f"{p}_{r}": lat.tune(p, r, 1, stream)
                                       for p, r in (("fp16", 12), ("fp64", 18), ("fp32", 12))}
-    lat.set_arith(args.arith)
     other = 48 - args.arith
 
     for _ in range(args.warmup):

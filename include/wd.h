@@ -365,6 +365,8 @@ typedef struct {
     int rhs_links_smem_reducing;  /* ... links in shared memory                               */
     double us16_reducing;         /* ... its average launch time, microseconds                */
     int candidates16;             /* FP16-arithmetic configurations timed per form            */
+    int sites_per_thread;         /* plain FP16-arithmetic hop with K = 1: sites per thread
+                                     chosen among 1, 2, 4 (grid-stride launch)                */
 } wd_tune_result;
 
 /* Autotune the hopping kernel H_eo (Eq. 1) of storage precision `prec` with
@@ -385,7 +387,8 @@ typedef struct {
  * per thread); for nrhs > 1 wd_tune then also times it with K right-hand
  * sides per thread (every divisor K of nrhs up to 12; the site's 8 links are
  * loaded once for its K right-hand sides, in registers or in shared memory)
- * and keeps the fastest K for each form (wd_set_rhs_per_thread sets them
+ * and, for K = 1, the plain hop with 1, 2 or 4 sites per thread, and keeps
+ * the fastest for each form (wd_set_rhs_per_thread sets K
  * directly); a batch of nrhs right-hand sides then uses the largest divisor
  * of nrhs up to that K. Not a feature of the paper. Synchronizes `stream`;
  * allocates three scratch vectors of nrhs parity vectors. `out` may be NULL. */

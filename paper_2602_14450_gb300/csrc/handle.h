@@ -68,6 +68,7 @@ struct wd_handle {
     // FP16-arithmetic hop chosen by wd_tune: right-hand sides per thread and links in shared memory
     int tune_rhs[2][2] = {};
     int tune_rhs_smem[2][2] = {};
+    int tune_spt[2] = {};              // ... sites per thread of the plain FP16-arithmetic hop
 
     int arith16 = 0;                   // wd_set_arith: FP16-storage hops sum in FP16 arithmetic
 
@@ -107,6 +108,7 @@ inline void apply_tuning(const wd_handle* h, int prec, int recon, HopParams& P) 
         P.rhs_group[f] = P.arith16 ? h->tune_rhs[recon == 12 ? 0 : 1][f] : 0;
         P.rhs_smem[f] = P.arith16 ? h->tune_rhs_smem[recon == 12 ? 0 : 1][f] : 0;
     }
+    P.spt = P.arith16 ? h->tune_spt[recon == 12 ? 0 : 1] : 0;
 }
 
 }  // namespace wd

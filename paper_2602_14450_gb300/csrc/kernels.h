@@ -44,6 +44,7 @@ struct HopParams {
     int rhs_group[2];          // FP16 arithmetic: right-hand sides per thread (hop16m_kernel) without / with a
                                // fused reduction; 0 or 1 = one (hop16_kernel); must divide nrhs to be used
     int rhs_smem[2];           // ... and 1 = the site's links in shared memory instead of registers
+    int spt;                   // FP16 arithmetic, plain hop: sites per thread (grid-stride; 0 or 1 = one site)
 };
 
 // Largest number of blocks a reducing kernel uses per right-hand side.

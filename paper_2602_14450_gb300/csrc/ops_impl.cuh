@@ -148,7 +148,9 @@ cudaError_t run_hop(const HopParams& P, cudaStream_t s) {
                 { const cudaError_t le_ = launch_k(hop16_kernel<R, E, D, false, 1>, nb * P.nrhs, blk, 0, s, Q); if (le_ != cudaSuccess) return le_; }
             } else {
                 const void* k = (const void*)hop16_kernel<R, E, D, false, 2>;
-                const int nb = (D == RED_NONE) ? stream_blocks(P.g.Vh, blk) : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
+                const int spt = P.spt > 1 ? P.spt : 1;             // sites per thread of the plain hop
+                const int nb = (D == RED_NONE) ? stream_blocks((P.g.Vh + spt - 1) / spt, blk)
+                                               : reduce_blocks(k, P.g.Vh, blk, P.nrhs);
                 { const cudaError_t le_ = launch_k(hop16_kernel<R, E, D, false, 2>, nb * P.nrhs, blk, 0, s, Q); if (le_ != cudaSuccess) return le_; }
             }
             return cudaGetLastError();

@@ -97,7 +97,7 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
     // FP16 arithmetic (wd_set_arith(16)): right-hand sides per thread of the FP16-arithmetic hop, K dividing
     // nrhs (K = 1: one per thread), the site's links in registers or in shared memory
     const int ri = recon == 12 ? 0 : 1;
-    int best_k[2] = {1, 1}, best_lsm[2] = {0, 0};
+    int best_k[2] = {1, 1}, best_lsm[2] = {0, 0}, best_spt = 1;
     float best16[2] = {1e30f, 1e30f};
     int cands16 = 0;
     if (prec == WD_FP16 && h->arith16 && err == cudaSuccess) {
@@ -107,9 +107,14 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
         for (int form = 0; form < 2 && err == cudaSuccess; ++form) {
             for (int k = 1; k <= 12 && err == cudaSuccess; ++k) {
                 if (nrhs % k) continue;
-                for (int lsm = 0; lsm < (k > 1 ? 2 : 1) && err == cudaSuccess; ++lsm) {
+                // K = 1: also 2 and 4 sites per thread for the plain hop (grid-stride)
+                const int nshape = k > 1 ? 2 : (form == 0 ? 3 : 1);
+                for (int shape = 0; shape < nshape && err == cudaSuccess; ++shape) {
+                    const int lsm = k > 1 ? shape : 0;
+                    const int spt = k > 1 ? 1 : (1 << shape);
                     P.rhs_group[form] = k;
                     P.rhs_smem[form] = lsm;
+                    P.spt = spt;
                     auto launch = [&]() {
                         return form == 0 ? Ops<__half>::hop(recon, EPI_H, RED_NONE, P, s)
                                          : Ops<__half>::hop(recon, EPI_Y, RED_TS, P, s);
@@ -128,6 +133,7 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
                         best16[form] = ms;
                         best_k[form] = k;
                         best_lsm[form] = lsm;
+                        if (form == 0) best_spt = spt;
                     }
                 }
             }
@@ -140,6 +146,7 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
         for (int form = 0; form < 2; ++form) {
             h->tune_rhs[ri][form] = best_k[form];
             h->tune_rhs_smem[ri][form] = best_lsm[form];
+            h->tune_spt[ri] = best_spt;
         }
     for (int form = 0; form < 2; ++form) {
         h->tune_variant[prec][ri][form] = best[form].variant;
@@ -163,6 +170,7 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
         out->rhs_links_smem_reducing = a16 ? best_lsm[1] : 0;
         out->us16_reducing = a16 ? 1e3 * best16[1] : 0.0;
         out->candidates16 = cands16;
+        out->sites_per_thread = a16 ? best_spt : 1;
     }
     return WD_OK;
 }

@@ -46,7 +46,7 @@ class TuneResult(C.Structure):
                 ("candidates", C.c_int), ("variant_reducing", C.c_int), ("block_reducing", C.c_int),
                 ("us_reducing", C.c_double), ("rhs_per_thread", C.c_int), ("rhs_links_smem", C.c_int),
                 ("us16", C.c_double), ("rhs_per_thread_reducing", C.c_int), ("rhs_links_smem_reducing", C.c_int),
-                ("us16_reducing", C.c_double), ("candidates16", C.c_int)]
+                ("us16_reducing", C.c_double), ("candidates16", C.c_int), ("sites_per_thread", C.c_int)]
 
 
 class SolveParams(C.Structure):
