@@ -99,6 +99,12 @@ def test_matvec_counts_match_emulated_oracle(smeared):
     # The oracle runs Alg. 3 + Alg. 4 with FP16 storage emulated on the same
     # inputs (and FP16 arithmetic where the GPU uses it); counts agree within
     # 15% (summation order and the FP32 parts of the GPU's arithmetic differ).
+    # With FP16 stencil arithmetic the trajectory follows the rounding order
+    # of the FP64 dot products: the oracle's own count for the rescaled row is
+    # 260 with one host's float64 summation order and 280 with another's, and
+    # 268-284 (232-252 unrescaled) when only its dot products are summed in
+    # permuted orders; with FP32 stencil arithmetic the same permutations move
+    # it by under 1%. Those rows are held to 20%.
     dims, u, eta, kappa = smeared
     lat = lattice(u, kappa, dims)
     b = lex_dev(eta)
@@ -117,8 +123,9 @@ def test_matvec_counts_match_emulated_oracle(smeared):
         st = lat.solve(b, x, TOL, scheme, params=p)
         assert st.status == wd.WD_OK
         _, tr = S.solve_wilson_mixed(u, eta, kappa, BC, fmt=fmt, outer=outer, inner=inner, arith16=arith == 16)
-        assert abs(st.inner_matvecs - tr.matvecs) <= 0.15 * tr.matvecs + 4, (scheme, arith, st.inner_matvecs,
-                                                                              tr.matvecs)
+        rel = 0.20 if arith == 16 else 0.15
+        assert abs(st.inner_matvecs - tr.matvecs) <= rel * tr.matvecs + 4, (scheme, arith, st.inner_matvecs,
+                                                                             tr.matvecs)
     lat.set_arith(32)
     # FP64 BiCGStab (Alg. 4 with gamma = 1) against the oracle's float64 run of the same recurrence
     x = torch.zeros_like(b)
