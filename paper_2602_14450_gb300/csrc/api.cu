@@ -104,8 +104,8 @@ int ensure_solver_state(wd_handle* h, int nrhs) {
         for (int i = 0; i < 2; ++i) WD_CUDA(h, cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming));
         WD_CUDA(h, cudaEventCreate(&h->t0));
         WD_CUDA(h, cudaEventCreate(&h->t1));
-        WD_CUDA(h, cudaMalloc(&h->dflag, sizeof(int)));
-        WD_CUDA(h, cudaMallocHost(&h->hflag, 2 * sizeof(int)));
+        WD_CUDA(h, cudaHostAlloc((void**)&h->hflag, sizeof(int), cudaHostAllocMapped));
+        WD_CUDA(h, cudaHostGetDevicePointer((void**)&h->dflag, h->hflag, 0));
     }
     if (h->cap_rhs >= nrhs) return WD_OK;
     WD_CUDA(h, cudaDeviceSynchronize());
@@ -253,7 +253,6 @@ int wd_destroy(wd_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : h->ws)
         if (kv.second.p) cudaFree(kv.second.p);
-    if (h->dflag) cudaFree(h->dflag);
     for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c)

@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) k_xr(int n, int nrhs, long long vs, uint4
             }
         }
     }
-    double v[4] = {(double)s_r2, (double)s_x2, (double)s_re, (double)s_im};
-    grid_reduce<4>(v, rc, sl);
+    const C v[4] = {s_r2, s_x2, s_re, s_im};
+    grid_reduce<4, ST_RFUSED>(v, rc, sl);
 }
 
 // r := (sigma / g) r, and x := lambda x when rescaling the solution (Alg. 5)
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, ui
             store_spinor<T>(x, n, h, xx, st->ftz);
         }
     }
-    double v[3] = {(double)s_r2, (double)s_re, (double)s_im};
-    grid_reduce<3>(v, rc, sl);
+    const C v[3] = {s_r2, s_re, s_im};
+    grid_reduce<3, ST_END>(v, rc, sl);
 }
 
 // Rescale the FP64 outer residual and demote it (Alg. 3, first lines):
@@ -302,6 +302,34 @@ template <> __device__ __forceinline__ double from_double<double>(double v) { re
 template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+// Exact widening of a storage value to the arithmetic type C of its unit.
+template <typename T>
+__device__ __forceinline__ typename Unit<T>::C widen(T v);
+template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
+template <> __device__ __forceinline__ float widen<float>(float v) { return v; }
+template <> __device__ __forceinline__ float widen<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Exact float -> double from the IEEE-754 bit fields on the integer pipe (the
+// FP64 pipe of this GPU is ~70x narrower than the FP32 and integer ones):
+// sign kept, exponent rebased from 127 to 1023, mantissa shifted into the top
+// of the 52-bit field; float subnormals are normalised, infinities and NaNs
+// keep the all-ones exponent.
+__device__ __forceinline__ double f32_to_f64(float a) {
+    const unsigned u = __float_as_uint(a);
+    const unsigned sgn = u & 0x80000000u;
+    unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    if (e == 0u) {
+        if (m == 0u) return __hiloint2double((int)sgn, 0);
+        const int p = 31 - __clz((int)m);   // leading bit of the subnormal: value = m 2^-149
+        m = (m << (23 - p)) & 0x7FFFFFu;
+        e = (unsigned)(p - 149 + 1023);
+    } else {
+        e = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+    }
+    return __hiloint2double((int)(sgn | (e << 20) | (m >> 3)), (int)(m << 29));
+}
 
 template <typename T>
 __device__ __forceinline__ double to_double(T v);
@@ -334,23 +362,26 @@ __global__ void __launch_bounds__(256) k_rescale_in(int n, int nrhs, long long v
     r += sl.rhs * vs;
     rstar += sl.rhs * vs;
     const double f = st->s / st->rnorm;
+    const C tiny = (C)(sizeof(T) == 2 ? 6.103515625e-05 : 1.1754943508222875e-38);   // flush threshold
     C s_n2 = 0;
-    double nz = 0;
+    int nz = 0;
     RHS_LOOP(h, n) {
         double src[24];
         load_spinor<double>(r64, n, h, src);
         alignas(16) T y[24];
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
+            // the product in FP64, rounded once to T; the rest on the exact widened value in C (a 16-bit
+            // value's square is exact in FP32, a float's is rounded once, as a double square cast to float)
             T v = from_double<T>(f * src[i]);
-            double dv = to_double<T>(v);
-            if (ftz && fabs(dv) < (sizeof(T) == 2 ? 6.103515625e-05 : 1.1754943508222875e-38)) {
+            C dv = widen<T>(v);
+            if (ftz && fabs(dv) < tiny) {
                 v = from_double<T>(0.0);
-                dv = 0.0;
+                dv = 0;
             }
             y[i] = v;
-            s_n2 += (C)(dv * dv);
-            nz += dv != 0.0 ? 1.0 : 0.0;
+            s_n2 += dv * dv;
+            nz += dv != (C)0 ? 1 : 0;
         }
 #pragma unroll
         for (int u = 0; u < 24 / N; ++u) {
@@ -359,8 +390,8 @@ __global__ void __launch_bounds__(256) k_rescale_in(int n, int nrhs, long long v
             rstar[(size_t)u * n + h] = w;
         }
     }
-    double v[2] = {(double)s_n2, nz};
-    grid_reduce<2>(v, rc, sl);
+    const C v[2] = {s_n2, (C)nz};   // a per-thread count (at most 24 per site) is exact in FP32
+    grid_reduce<2, ST_INIT>(v, rc, sl);
 }
 
 // out = M in site by site (M: 12 x 12 complex blocks of one parity, shared by all right-hand sides)
@@ -473,7 +504,10 @@ __global__ void __launch_bounds__(256) k_correct(int n, int nrhs, long long vs, 
 #pragma unroll
         for (int e = 0; e < 24; ++e) {
             double* xp = elem_ptr<double>(x64, n, h, e);
-            *xp += f * to_double<T>(*elem_ptr<T>(xt, n, h, e));
+            if constexpr (sizeof(T) == 8)
+                *xp += f * to_double<T>(*elem_ptr<T>(xt, n, h, e));
+            else   // the FP32 widening of a 16- or 32-bit value, made double on the integer pipe
+                *xp += f * f32_to_f64((float)widen<T>(*elem_ptr<T>(xt, n, h, e)));
         }
     }
 }
@@ -492,7 +526,7 @@ __global__ void __launch_bounds__(256) k_norm2(int n, int nrhs, long long vs, co
 #pragma unroll
         for (int i = 0; i < 24; ++i) s += a[i] * a[i];
     }
-    double d[1] = {(double)s};
+    const C d[1] = {s};
     grid_reduce<1>(d, rc, sl);
 }
 
@@ -511,7 +545,13 @@ __global__ void k_unpack(Geom g, int parity, const uint4* in, double* lex) {
     GRID_STRIDE(h, g.Vh) {
         const int s = lex_of(g, parity, h);
 #pragma unroll
-        for (int e = 0; e < 24; ++e) lex[(size_t)s * 24 + e] = to_double<T>(*elem_ptr<T>(in, g.Vh, h, e));
+        for (int e = 0; e < 24; ++e) {
+            const T v = *elem_ptr<T>(in, g.Vh, h, e);
+            if constexpr (sizeof(T) == 8)
+                lex[(size_t)s * 24 + e] = to_double<T>(v);
+            else
+                lex[(size_t)s * 24 + e] = f32_to_f64((float)widen<T>(v));
+        }
     }
 }
 

@@ -397,171 +397,204 @@ enum Stage {
     ST_RFUSED = 9    // sums: |r|^2, |r_st|^2, (r*, r_st) -> gamma, beta, convergence (rescaling fused)
 };
 
-__device__ __forceinline__ bool finite2(const double* z) { return isfinite(z[0]) && isfinite(z[1]); }
-
-__device__ __forceinline__ void cdiv(const double* a, const double* b, double* out) {
-    double d = b[0] * b[0] + b[1] * b[1];
-    double re = (a[0] * b[0] + a[1] * b[1]) / d;
-    double im = (a[1] * b[0] - a[0] * b[1]) / d;
-    out[0] = re;
-    out[1] = im;
-}
-__device__ __forceinline__ void cmul(const double* a, const double* b, double* out) {
-    double re = a[0] * b[0] - a[1] * b[1];
-    double im = a[0] * b[1] + a[1] * b[0];
-    out[0] = re;
-    out[1] = im;
-}
-
 // Status codes (mirror enum wd_status of wd.h).
 enum { S_OK = 0, S_NOT_CONVERGED = 4, S_BREAKDOWN = 5, S_NONFINITE = 6 };
 
-__device__ inline void stop(SolverState* st, int status) {
+__device__ __forceinline__ void stop(SolverState* st, int status) {
     st->done = 1;
     if (st->status == S_OK) st->status = status;
 }
 
+// The stages below run in one thread at the end of a reducing kernel, on
+// the critical path between two kernels. FP64 is slow on this GPU (64 cycles
+// for a dependent add or FMA, ~560 for a division or a square root), so each
+// stage reads the state it needs into registers before any branch (one
+// round trip to memory), divides once where a reciprocal serves several
+// products, and stores only what it changes.
+
 // End of a BiCGStab iteration (Alg. 4 last lines): gamma known, r stored.
 // rn2 = |r_stored|^2, rs = (r*, r_stored).
-__device__ inline void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
-    double rho_new[2] = {rs[0], rs[1]};
-    // rho' = gamma * rho, gamma' *= gamma, alpha' = alpha, omega' = omega
-    st->rho_p[0] = gamma * st->rho[0];
-    st->rho_p[1] = gamma * st->rho[1];
-    st->gamma_p *= gamma;
-    st->alpha_p[0] = st->alpha[0]; st->alpha_p[1] = st->alpha[1];
-    st->omega_p[0] = st->omega[0]; st->omega_p[1] = st->omega[1];
-    if (st->rescale_x) st->lambda_p *= st->lam;
-    st->rho[0] = rho_new[0];
-    st->rho[1] = rho_new[1];
-    // beta = rho alpha' / (rho' omega'); p-update folds the gamma of p and v.
-    double num[2], den[2], beta[2];
-    cmul(st->rho, st->alpha_p, num);
-    cmul(st->rho_p, st->omega_p, den);
-    cdiv(num, den, beta);
-    st->cP[0] = gamma * beta[0];
-    st->cP[1] = gamma * beta[1];
-    cmul(st->cP, st->omega_p, st->cV);
-    st->iter += 1;
-    st->matvecs += 2;
+__device__ __forceinline__ void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
+    const double rho0 = st->rho[0], rho1 = st->rho[1];
+    const double al0 = st->alpha[0], al1 = st->alpha[1], om0 = st->omega[0], om1 = st->omega[1];
+    const double gp = st->gamma_p * gamma;
+    const double lp = st->rescale_x ? st->lambda_p * st->lam : st->lambda_p;
+    const int iter = st->iter + 1, matvecs = st->matvecs + 2, status = st->status;
+    const double eps_b = st->eps * st->bnorm;
+    const int max_mv = st->max_matvecs, hist_cap = st->hist_cap;
+    double* hist = st->hist;
+    // rho' = gamma * rho, gamma' *= gamma, alpha' = alpha, omega' = omega, rho = (r*, r)
+    const double rp0 = gamma * rho0, rp1 = gamma * rho1;
+    // beta = rho alpha' / (rho' omega'); the p-update folds the gamma of p and v: cP = gamma beta, cV = cP omega'.
+    // With rho' = gamma rho_old, cP = rho alpha' / (rho_old omega'): formed without waiting for gamma.
+    const double n0 = rs[0] * al0 - rs[1] * al1, n1 = rs[0] * al1 + rs[1] * al0;
+    const double d0 = rho0 * om0 - rho1 * om1, d1 = rho0 * om1 + rho1 * om0;
+    const double id = 1.0 / (d0 * d0 + d1 * d1);
+    const double cp0 = (n0 * d0 + n1 * d1) * id, cp1 = (n1 * d0 - n0 * d1) * id;
+    const double cv0 = cp0 * om0 - cp1 * om1, cv1 = cp0 * om1 + cp1 * om0;
+    const double res = sqrt(rn2) / gp;
+    st->rho_p[0] = rp0; st->rho_p[1] = rp1;
+    st->gamma_p = gp;
+    st->alpha_p[0] = al0; st->alpha_p[1] = al1;
+    st->omega_p[0] = om0; st->omega_p[1] = om1;
+    st->lambda_p = lp;
+    st->rho[0] = rs[0]; st->rho[1] = rs[1];
+    st->cP[0] = cp0; st->cP[1] = cp1;
+    st->cV[0] = cv0; st->cV[1] = cv1;
+    st->iter = iter;
+    st->matvecs = matvecs;
     st->first = 0;
-    st->res = sqrt(rn2) / st->gamma_p;
-    if (st->hist && st->iter <= st->hist_cap) {
-        st->hist[2 * (st->iter - 1)] = (double)st->matvecs;
-        st->hist[2 * (st->iter - 1) + 1] = st->res;
+    st->res = res;
+    if (hist && iter <= hist_cap) {
+        hist[2 * (iter - 1)] = (double)matvecs;
+        hist[2 * (iter - 1) + 1] = res;
     }
-    if (!(isfinite(st->res) && finite2(st->cP) && finite2(st->cV) && isfinite(st->gamma_p))) {
-        stop(st, S_NONFINITE);
-        return;
+    int stop_with = -1;
+    if (!(isfinite(res) && isfinite(cp0) && isfinite(cp1) && isfinite(cv0) && isfinite(cv1) && isfinite(gp)))
+        stop_with = S_NONFINITE;
+    else if (res <= eps_b)
+        stop_with = S_OK;
+    else if (matvecs >= max_mv)
+        stop_with = S_NOT_CONVERGED;
+    else if ((d0 == 0.0 && d1 == 0.0) || gamma == 0.0)   // rho' omega' = 0
+        stop_with = S_BREAKDOWN;
+    if (stop_with >= 0) {
+        st->done = 1;
+        if (status == S_OK) st->status = stop_with;
     }
-    if (st->res <= st->eps * st->bnorm) { stop(st, S_OK); return; }
-    if (st->matvecs >= st->max_matvecs) { stop(st, S_NOT_CONVERGED); return; }
-    if (den[0] == 0.0 && den[1] == 0.0) stop(st, S_BREAKDOWN);
 }
 
-// Scalar work done by the last block of a reducing kernel, one thread.
-__device__ inline void run_stage(int stage, const double* s, SolverState* st) {
+// Scalar work done by the last block of a reducing kernel, one thread: one
+// function per stage; a kernel inlines the stage it expects (its code then
+// follows the final sum in instruction memory) and calls the shared
+// out-of-line dispatcher for any other.
+template <int STAGE> __device__ __forceinline__ void stage_fn(const double* s, SolverState* st) {}
+
+template <> __device__ __forceinline__ void stage_fn<ST_INIT>(const double* s, SolverState* st) {
+    double n2 = s[0];
+    st->shat = sqrt(n2);
+    st->nonzeros = (long long)s[1];
+    st->bnorm = st->use_shat ? st->shat : st->s;
+    // Alg. 4 start: r = r* = y~, p = v = 0, rho' = |r|^2, omega' = alpha' = gamma' = 1
+    st->rho[0] = n2; st->rho[1] = 0;
+    st->rho_p[0] = n2; st->rho_p[1] = 0;
+    st->alpha_p[0] = 1; st->alpha_p[1] = 0;
+    st->omega_p[0] = 1; st->omega_p[1] = 0;
+    st->cP[0] = st->cP[1] = st->cV[0] = st->cV[1] = 0;
+    st->gamma_p = 1;
+    st->lambda_p = 1;
+    st->lam = 1;
+    st->iter = 0;
+    st->matvecs = 0;
+    st->first = 1;
+    st->done = 0;
+    st->status = S_OK;
+    st->res = st->shat;
+    if (!(n2 > 0) || !isfinite(n2)) stop(st, isfinite(n2) ? S_OK : S_NONFINITE);
+}
+
+template <> __device__ __forceinline__ void stage_fn<ST_ALPHA>(const double* s, SolverState* st) {   // alpha = rho / (r*, v)
+    const double rho0 = st->rho[0], rho1 = st->rho[1];
+    const double v0 = s[0], v1 = s[1];
+    if (!(isfinite(v0) && isfinite(v1))) { stop(st, S_NONFINITE); return; }
+    if (v0 == 0.0 && v1 == 0.0) { stop(st, S_BREAKDOWN); return; }
+    const double id = 1.0 / (v0 * v0 + v1 * v1);
+    st->alpha[0] = (rho0 * v0 + rho1 * v1) * id;
+    st->alpha[1] = (rho1 * v0 - rho0 * v1) * id;
+}
+
+// omega = (t, s) / (t, t) with the omega_0 prescription; with fused rescaling also the factor for r
+template <> __device__ __forceinline__ void stage_fn<ST_OMEGA>(const double* s, SolverState* st) {
+    const double omega0 = st->omega0, sigma = st->sigma;
+    const double c = st->lambda_p / st->gamma_p;
+    const double al0 = st->alpha[0], al1 = st->alpha[1];
+    const int fused = st->fused_scale;
+    const double ts0 = s[0], ts1 = s[1], tt = s[2], ss = s[3];
+    if (!(isfinite(tt) && isfinite(ss) && isfinite(ts0) && isfinite(ts1))) { stop(st, S_NONFINITE); return; }
+    if (tt == 0.0) { stop(st, S_BREAKDOWN); return; }
+    const double itt = 1.0 / tt;
+    // |omega^| = |(t, s)| / (|t| |s|) below omega0: omega *= omega0 / |omega^| (compared squared; the factor
+    // is formed alongside 1 / (t, t) and selected)
+    const double a2 = ts0 * ts0 + ts1 * ts1, q = tt * ss;
+    const double fs = omega0 * sqrt(q / a2);
+    const double f = (omega0 > 0.0 && a2 > 0.0 && a2 < omega0 * omega0 * q) ? fs : 1.0;
+    const double om0 = ts0 * itt * f, om1 = ts1 * itt * f;
+    st->omega[0] = om0;
+    st->omega[1] = om1;
+    if (fused) {
+        // |s - omega t|^2 = (s,s) - 2 Re(conj(omega) (t,s)) + |omega|^2 (t,t), floored against
+        // cancellation; the factor sigma / g~ rescales r as it is stored
+        double r2 = ss - 2.0 * (om0 * ts0 + om1 * ts1) + (om0 * om0 + om1 * om1) * tt;
+        r2 = fmax(r2, 1e-12 * ss);
+        const double gt = sigma * rsqrt(r2);
+        st->gam_tmp = gt;
+        if (!isfinite(gt)) { stop(st, S_NONFINITE); return; }
+    }
+    st->cXr[0] = c * om0;
+    st->cXr[1] = c * om1;
+    st->cXp[0] = c * al0;
+    st->cXp[1] = c * al1;
+}
+
+template <> __device__ __forceinline__ void stage_fn<ST_RNORM>(const double* s, SolverState* st) {
+    double r2 = s[0], x2 = s[1];
+    double rs[2] = {s[2], s[3]};
+    st->g = sqrt(r2);
+    if (st->rescale_x) st->lam = st->sigma_lambda / sqrt(x2);
+    if (st->scale_pass) {
+        st->gam_tmp = st->sigma > 0.0 ? st->sigma / st->g : 1.0;
+        if (!isfinite(st->gam_tmp) || (st->rescale_x && !isfinite(st->lam))) stop(st, S_NONFINITE);
+    } else {
+        end_iteration(st, 1.0, r2, rs);
+    }
+}
+
+template <> __device__ __forceinline__ void stage_fn<ST_END>(const double* s, SolverState* st) {
+    double rn2 = s[0];
+    double rs[2] = {s[1], s[2]};
+    double gamma = st->sigma > 0.0 ? (st->recalc ? sqrt(rn2) / st->g : st->gam_tmp) : 1.0;
+    end_iteration(st, gamma, rn2, rs);
+}
+
+template <> __device__ __forceinline__ void stage_fn<ST_RFUSED>(const double* s, SolverState* st) {
+    const int recalc = st->recalc;
+    const double gt = st->gam_tmp;
+    const double r2 = s[0], rn2 = s[1];
+    const double rs[2] = {s[2], s[3]};
+    const double g = sqrt(r2);
+    st->g = g;
+    double gamma = recalc ? sqrt(rn2) / g : gt;
+    if (r2 == 0.0) gamma = 1.0;   // r = 0 exactly: nothing was scaled, the solve has converged
+    end_iteration(st, gamma, rn2, rs);
+}
+
+template <> __device__ __forceinline__ void stage_fn<ST_OUTER>(const double* s, SolverState* st) { st->rnorm = sqrt(s[0]); }
+
+template <> __device__ __forceinline__ void stage_fn<ST_ACC>(const double* s, SolverState* st) { st->acc += s[0]; }
+
+template <> __device__ __forceinline__ void stage_fn<ST_ACC_SET>(const double* s, SolverState* st) { st->acc = s[0]; }
+
+static __device__ __noinline__ void run_stage(int stage, const double* s, SolverState* st) {
     switch (stage) {
-    case ST_INIT: {
-        double n2 = s[0];
-        st->shat = sqrt(n2);
-        st->nonzeros = (long long)s[1];
-        st->bnorm = st->use_shat ? st->shat : st->s;
-        // Alg. 4 start: r = r* = y~, p = v = 0, rho' = |r|^2, omega' = alpha' = gamma' = 1
-        st->rho[0] = n2; st->rho[1] = 0;
-        st->rho_p[0] = n2; st->rho_p[1] = 0;
-        st->alpha_p[0] = 1; st->alpha_p[1] = 0;
-        st->omega_p[0] = 1; st->omega_p[1] = 0;
-        st->cP[0] = st->cP[1] = st->cV[0] = st->cV[1] = 0;
-        st->gamma_p = 1;
-        st->lambda_p = 1;
-        st->lam = 1;
-        st->iter = 0;
-        st->matvecs = 0;
-        st->first = 1;
-        st->done = 0;
-        st->status = S_OK;
-        st->res = st->shat;
-        if (!(n2 > 0) || !isfinite(n2)) stop(st, isfinite(n2) ? S_OK : S_NONFINITE);
-        break;
+    case ST_INIT: stage_fn<ST_INIT>(s, st); break;
+    case ST_ALPHA: stage_fn<ST_ALPHA>(s, st); break;
+    case ST_OMEGA: stage_fn<ST_OMEGA>(s, st); break;
+    case ST_RNORM: stage_fn<ST_RNORM>(s, st); break;
+    case ST_END: stage_fn<ST_END>(s, st); break;
+    case ST_RFUSED: stage_fn<ST_RFUSED>(s, st); break;
+    case ST_OUTER: stage_fn<ST_OUTER>(s, st); break;
+    case ST_ACC: stage_fn<ST_ACC>(s, st); break;
+    case ST_ACC_SET: stage_fn<ST_ACC_SET>(s, st); break;
+    default: break;
     }
-    case ST_ALPHA: {
-        double rv[2] = {s[0], s[1]};
-        if (!finite2(rv)) { stop(st, S_NONFINITE); break; }
-        if (rv[0] == 0.0 && rv[1] == 0.0) { stop(st, S_BREAKDOWN); break; }
-        cdiv(st->rho, rv, st->alpha);
-        break;
-    }
-    case ST_OMEGA: {
-        double ts[2] = {s[0], s[1]};
-        double tt = s[2], ss = s[3];
-        if (!(isfinite(tt) && isfinite(ss) && finite2(ts))) { stop(st, S_NONFINITE); break; }
-        if (tt == 0.0) { stop(st, S_BREAKDOWN); break; }
-        double om[2] = {ts[0] / tt, ts[1] / tt};
-        double ohat = sqrt(ts[0] * ts[0] + ts[1] * ts[1]) / sqrt(tt * ss);
-        if (ohat < st->omega0 && ohat > 0.0) {
-            double f = st->omega0 / ohat;
-            om[0] *= f;
-            om[1] *= f;
-        }
-        st->omega[0] = om[0];
-        st->omega[1] = om[1];
-        if (st->fused_scale) {
-            // |s - omega t|^2 = (s,s) - 2 Re(conj(omega) (t,s)) + |omega|^2 (t,t), floored against
-            // cancellation; the factor sigma / g~ rescales r as it is stored
-            double r2 = ss - 2.0 * (om[0] * ts[0] + om[1] * ts[1]) + (om[0] * om[0] + om[1] * om[1]) * tt;
-            r2 = fmax(r2, 1e-12 * ss);
-            st->gam_tmp = st->sigma / sqrt(r2);
-            if (!isfinite(st->gam_tmp)) { stop(st, S_NONFINITE); break; }
-        }
-        double c = st->lambda_p / st->gamma_p;
-        st->cXr[0] = c * om[0];
-        st->cXr[1] = c * om[1];
-        st->cXp[0] = c * st->alpha[0];
-        st->cXp[1] = c * st->alpha[1];
-        break;
-    }
-    case ST_RNORM: {
-        double r2 = s[0], x2 = s[1];
-        double rs[2] = {s[2], s[3]};
-        st->g = sqrt(r2);
-        if (st->rescale_x) st->lam = st->sigma_lambda / sqrt(x2);
-        if (st->scale_pass) {
-            st->gam_tmp = st->sigma > 0.0 ? st->sigma / st->g : 1.0;
-            if (!isfinite(st->gam_tmp) || (st->rescale_x && !isfinite(st->lam))) stop(st, S_NONFINITE);
-        } else {
-            end_iteration(st, 1.0, r2, rs);
-        }
-        break;
-    }
-    case ST_END: {
-        double rn2 = s[0];
-        double rs[2] = {s[1], s[2]};
-        double gamma = st->sigma > 0.0 ? (st->recalc ? sqrt(rn2) / st->g : st->gam_tmp) : 1.0;
-        end_iteration(st, gamma, rn2, rs);
-        break;
-    }
-    case ST_RFUSED: {
-        double r2 = s[0], rn2 = s[1];
-        double rs[2] = {s[2], s[3]};
-        st->g = sqrt(r2);
-        double gamma = st->recalc ? sqrt(rn2) / st->g : st->gam_tmp;
-        if (r2 == 0.0) gamma = 1.0;   // r = 0 exactly: nothing was scaled, the solve has converged
-        end_iteration(st, gamma, rn2, rs);
-        break;
-    }
-    case ST_OUTER:
-        st->rnorm = sqrt(s[0]);
-        break;
-    case ST_ACC:
-        st->acc += s[0];
-        break;
-    case ST_ACC_SET:
-        st->acc = s[0];
-        break;
-    default:
-        break;
-    }
+}
+
+template <int HINT>
+__device__ __forceinline__ void run_stage_hinted(int stage, const double* s, SolverState* st) {
+    if (HINT != ST_NONE && stage == HINT)
+        stage_fn<HINT>(s, st);
+    else
+        run_stage(stage, s, st);
 }
 
 // ----------------------------------------------------------- reductions ---
@@ -604,7 +637,9 @@ __device__ __forceinline__ void warp_sum(double (&v)[NSUM]) {
     }
 }
 
-// Sum v over the block; the result is valid in thread 0.
+// Sum v over the block; the result is valid in thread 0. FP64 additions are
+// slow on this GPU (64 cycles of latency each), so the second level adds the
+// few warp sums one after the other instead of another five-step shuffle.
 template <int NSUM>
 __device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
     __shared__ double sh[NSUM][32];
@@ -616,19 +651,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
         for (int k = 0; k < NSUM; ++k) sh[k][warp] = v[k];
     }
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
 #pragma unroll
-        for (int k = 0; k < NSUM; ++k) v[k] = lane < nw ? sh[k][lane] : 0.0;
-        warp_sum<NSUM>(v);
+            for (int k = 0; k < NSUM; ++k) v[k] += sh[k][w];
+        }
     }
 }
 
-// Reduce v over the sl.nb blocks that serve right-hand side sl.rhs.
-template <int NSUM>
-__device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc, const Slice& sl) {
+// Reduce v over the sl.nb blocks that serve right-hand side sl.rhs (HINT: the
+// scalar stage the calling kernel expects to run). The last block adds the partial sums with all its threads (each thread loads its
+// eight next partials before adding them, so the loads overlap), then sums
+// over the block; FP64 arithmetic is shared by the SM's warps, so spreading it
+// over the block's warps matters more than its latency.
+template <int NSUM, int HINT = ST_NONE>
+__device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const RedCtx& rc, const Slice& sl) {
     __shared__ unsigned is_last;
     double* part = rc.partials + (size_t)sl.rhs * RED_STRIDE;
     unsigned* ticket = rc.ticket + sl.rhs;
+    double v[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) v[k] = vin[k];
     block_sum<NSUM>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -642,13 +685,135 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NSUM], const RedCtx& rc,
     double acc[NSUM];
 #pragma unroll
     for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < sl.nb; b += blockDim.x) {
+    const int nt = blockDim.x;
+    for (int b0 = threadIdx.x; b0 < sl.nb; b0 += 8 * nt) {
+        double t[8][NSUM];
 #pragma unroll
-        for (int k = 0; k < NSUM; ++k) acc[k] += __ldcg(part + (size_t)b * NSUM + k);
+        for (int i = 0; i < 8; ++i) {
+            const int b = b0 + i * nt;
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) t[i][k] = b < sl.nb ? __ldcg(part + (size_t)b * NSUM + k) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) acc[k] += t[i][k];
     }
     block_sum<NSUM>(acc);
     if (threadIdx.x == 0) {
-        if (rc.st) run_stage(rc.stage, acc, rc.st + sl.rhs);
+        if (rc.st) run_stage_hinted<HINT>(rc.stage, acc, rc.st + sl.rhs);
+        *ticket = 0u;
+        __threadfence();
+    }
+}
+
+// Double-float reduction of FP32 per-thread partial sums. The partial sums of
+// the low-precision kernels are FP32; their block and grid sums are carried
+// as pairs (hi, lo) of FP32 numbers whose exact sum is the value, with the
+// error-free additions below, which run on the FP32 pipe (the FP64 pipe of this
+// GPU takes ~19 cycles per warp instruction per SM, and FP64 shuffle trees over
+// a block's warps made the reductions a visible share of every reducing
+// kernel). A pair carries ~48 significant bits, more than the FP32 partials it
+// adds; the order of the additions is fixed, so results are reproducible.
+struct F2 {
+    float hi, lo;
+};
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e == a + b exactly in round-to-nearest.
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// Fast2Sum (Dekker 1971): exact when |a| >= |b|.
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// x + y: the accurate double-word addition (sums of the high and of the low
+// words by TwoSum, each followed by a renormalisation; Hida, Li and Bailey 2001).
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    F2 s = two_sum(x.hi, y.hi);
+    const F2 t = two_sum(x.lo, y.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+template <int NSUM>
+__device__ __forceinline__ void warp_sum(F2 (&v)[NSUM]) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) {
+            const F2 o = {__shfl_down_sync(0xffffffffu, v[k].hi, off), __shfl_down_sync(0xffffffffu, v[k].lo, off)};
+            v[k] = f2_add(v[k], o);
+        }
+    }
+}
+
+// Sum of F2 values over the block, valid in thread 0.
+template <int NSUM>
+__device__ __forceinline__ void block_sum(F2 (&v)[NSUM]) {
+    __shared__ float2 shf[NSUM][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_sum<NSUM>(v);
+    __syncthreads();   // shf may still be read by a previous call
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) shf[k][warp] = make_float2(v[k].hi, v[k].lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) v[k] = f2_add(v[k], F2{shf[k][w].x, shf[k][w].y});
+        }
+    }
+}
+
+// grid_reduce for FP32 per-thread partial sums: block sums stored as FP32
+// pairs in the partial-sum slots; the last block sums them with the same code
+// that formed its own block sum (a second pass of one loop, so those
+// instructions are already in its SM's instruction cache: code that only the
+// last block runs costs instruction fetches from memory on the critical path)
+// and widens the pair's exact value to FP64 for the scalar stage.
+template <int NSUM, int HINT = ST_NONE>
+__device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCtx& rc, const Slice& sl) {
+    __shared__ unsigned is_last;
+    float2* part = reinterpret_cast<float2*>(rc.partials + (size_t)sl.rhs * RED_STRIDE);
+    unsigned* ticket = rc.ticket + sl.rhs;
+    F2 v[NSUM];
+#pragma unroll
+    for (int k = 0; k < NSUM; ++k) v[k] = F2{vf[k], 0.f};
+#pragma unroll 1
+    for (int pass = 0;; ++pass) {
+        block_sum<NSUM>(v);
+        if (pass == 1) break;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = make_float2(v[k].hi, v[k].lo);
+            __threadfence();
+            is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) v[k] = F2{0.f, 0.f};
+#pragma unroll 3
+        for (int b = threadIdx.x; b < sl.nb; b += blockDim.x) {
+            float2 t[NSUM];
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) t[k] = __ldcg(part + (size_t)b * NSUM + k);
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) v[k] = f2_add(v[k], F2{t[k].x, t[k].y});
+        }
+    }
+    if (threadIdx.x == 0) {
+        double a[NSUM];
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) a[k] = (double)v[k].hi + (double)v[k].lo;
+        if (rc.st) run_stage_hinted<HINT>(rc.stage, a, rc.st + sl.rhs);
         *ticket = 0u;
         __threadfence();
     }

@@ -45,8 +45,9 @@ struct wd_handle {
     int cap_rhs = 0;                   // right-hand sides the state arrays hold
     wd::SolverState* st = nullptr;     // device scalar state, one per right-hand side
     wd::SolverState* hst = nullptr;    // pinned host mirror
-    int* dflag = nullptr;              // device: "some right-hand side still iterating"
-    int* hflag = nullptr;              // pinned: copies of dflag of in-flight graph launches
+    int* hflag = nullptr;              // mapped pinned host word: "some right-hand side still iterating",
+                                       // written by the last kernel of each inner-iteration graph launch
+    int* dflag = nullptr;              // its device address
     double* partials = nullptr;        // reduction partials, RED_STRIDE per right-hand side
     unsigned* ticket = nullptr;        // reduction tickets, one per right-hand side
     cudaStream_t cap = nullptr;        // capture stream

@@ -264,12 +264,7 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT, AHEAD>::THREADS, Hop1
         }
     }
 
-    if constexpr (RED != RED_NONE) {
-        double v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc, sl);
-    }
+    if constexpr (RED != RED_NONE) grid_reduce<NS, RedStage<RED>::HINT>(part, P.rc, sl);
 }
 
 }  // namespace wd

@@ -186,14 +186,14 @@ __global__ void __launch_bounds__(128) hop16m_kernel(const HopParams P) {
     if constexpr (RED != RED_NONE) {
         for (int j = 0; j < K; ++j) {
             if (!((active >> j) & 1u)) continue;
-            double v[NS];
+            float v[NS];
 #pragma unroll
-            for (int k = 0; k < NS; ++k) v[k] = (double)s_part[(j * NS + k) * SH::THREADS + tid];
+            for (int k = 0; k < NS; ++k) v[k] = s_part[(j * NS + k) * SH::THREADS + tid];
             Slice sl;
             sl.rhs = r0 + j;
             sl.b = b;
             sl.nb = nb;
-            grid_reduce<NS>(v, P.rc, sl);
+            grid_reduce<NS, RedStage<RED>::HINT>(v, P.rc, sl);
         }
     }
 }

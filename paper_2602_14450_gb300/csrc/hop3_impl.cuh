@@ -266,10 +266,7 @@ __global__ void __launch_bounds__(128) hop3_kernel(const HopParams P, const Stag
     }
 
     if constexpr (RED != RED_NONE) {
-        double v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc, sl);
+        grid_reduce<NS, RedStage<RED>::HINT>(part, P.rc, sl);   // FP32 or FP64 partials, as the arithmetic
     }
 }
 

@@ -32,6 +32,10 @@ template <int RED> struct RedSums { static constexpr int N = 1; };
 template <> struct RedSums<RED_RSV> { static constexpr int N = 2; };
 template <> struct RedSums<RED_TS> { static constexpr int N = 4; };
 template <> struct RedSums<RED_NORM> { static constexpr int N = 1; };
+// The scalar stage a reducing hop runs at its end in the solvers.
+template <int RED> struct RedStage {
+    static constexpr int HINT = RED == RED_RSV ? ST_ALPHA : RED == RED_TS ? ST_OMEGA : RED == RED_NORM ? ST_OUTER : ST_NONE;
+};
 
 #define RE(s, c) (2 * (3 * (s) + (c)))
 #define IM(s, c) (2 * (3 * (s) + (c)) + 1)
@@ -471,10 +475,7 @@ __global__ void __launch_bounds__(HopBounds<T, RED, PF, MAT>::THREADS, HopBounds
     }
 
     if constexpr (RED != RED_NONE) {
-        double v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc, sl);
+        grid_reduce<NS, RedStage<RED>::HINT>(part, P.rc, sl);   // FP32 or FP64 partials, as the arithmetic
     }
 }
 
@@ -626,10 +627,7 @@ __global__ void __launch_bounds__(RingFmt<T, R>::BLOCK, 6) hop_ring_kernel(const
     cp_async_wait<0>();
 
     if constexpr (RED != RED_NONE) {
-        double v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) v[k] = (double)part[k];
-        grid_reduce<NS>(v, P.rc, sl);
+        grid_reduce<NS, RedStage<RED>::HINT>(part, P.rc, sl);   // FP32 or FP64 partials, as the arithmetic
     }
 }
 

@@ -49,10 +49,13 @@ static bool scheme_cfg(int scheme, SchemeCfg* c) {
 }
 
 // Flag "some right-hand side of this system is still in its inner solve".
-__global__ void k_any_active(int nrhs, const SolverState* st, int* flag) {
+// flag := "some right-hand side of the system is still iterating" (or_in = 0), or
+// flag |= it (or_in = 1: the systems after the first of a batch).
+__global__ void k_any_active(int nrhs, const SolverState* st, int* flag, int or_in) {
     const int r = threadIdx.x;
     const bool act = r < nrhs && !st[r].done && !st[r].skip;
-    if (__syncthreads_or(act) && r == 0) *flag = 1;
+    const int any = __syncthreads_or(act) ? 1 : 0;
+    if (r == 0 && (any || !or_in)) *(volatile int*)flag = any;
 }
 
 // Device buffers of one system for one call.
@@ -256,10 +259,8 @@ static int capture_inner(std::vector<Sys>& sys, int prec, int recon, int xr_mode
             for (auto& S : sys)
                 if (e == cudaSuccess) e = enqueue_iteration(S, prec, recon, xr_mode, learned, h0->cap);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(h0->dflag, 0, sizeof(int), h0->cap);
-    for (auto& S : sys) {
-        if (e != cudaSuccess) break;
-        k_any_active<<<1, 1024, 0, h0->cap>>>(S.nrhs, S.h->st, h0->dflag);
+    for (size_t i = 0; i < sys.size() && e == cudaSuccess; ++i) {   // the activity flag, in mapped host memory
+        k_any_active<<<1, 1024, 0, h0->cap>>>(sys[i].nrhs, sys[i].h->st, h0->dflag, i > 0 ? 1 : 0);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(h0->cap, &graph);
@@ -492,16 +493,17 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             WD_CUDA(S.h, e);
             nk += 1;
         }
-        // inner BiCGStab of all systems: graph launches, activity flag read one launch behind
+        // inner BiCGStab of all systems: graph launches, the activity flag read one launch behind (once
+        // launch kk - 1 has completed the mapped flag holds its value or a later launch's; within a trip the
+        // flag only falls from 1 to 0, so a later value is the more recent answer)
         const int max_launch = prm.max_inner / (2 * ips) + 3;
         for (int kk = 0;; ++kk) {
             WD_CUDA(h0, cudaGraphLaunch(exec, s));
             nk += graph_kernels;
-            WD_CUDA(h0, cudaMemcpyAsync(&h0->hflag[kk & 1], h0->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
             WD_CUDA(h0, cudaEventRecord(h0->ev[kk & 1], s));
             if (kk >= 1) {
                 WD_CUDA(h0, cudaEventSynchronize(h0->ev[(kk - 1) & 1]));
-                if (!h0->hflag[(kk - 1) & 1]) break;
+                if (!*(volatile int*)h0->hflag) break;
             }
             if (kk + 1 >= max_launch) break;
         }
