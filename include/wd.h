@@ -466,6 +466,21 @@ int wd_precond_train_step(wd_handle* h, int n, const float* v, const float* y, d
  * at least 4 * 8 * SMs bytes the kernel may write. */
 int wd_fma_probe(int bits, long long iters, void* sink, void* stream, double* flops);
 
+/* Kernel timeline (not a feature of the paper; the library built with
+ * -DWD_TIMELINE, libwd_timeline.so): from this call on, every block of the
+ * solvers' hopping and vector kernels appends one record of four 64-bit words
+ * to `blocks` and the last block of every grid reduction one record of ten
+ * words to `phases` (device buffers owned by the caller; word 0 of each is
+ * the record count, set it to 0; at most 2^24 block and 2^20 reduction
+ * records are kept). Block record: (source line | kernel tag << 12 |
+ * file-name hash << 16) << 32 | grid size << 8 | SM (the tag tells a hop's
+ * reductions apart), then the global-timer nanoseconds of the block's
+ * arrival, of its start after the wait for the preceding kernel, and of its
+ * end. Reduction record: stage << 32 | sums, then eight phase times and the
+ * end. NULL, NULL stops the recording. The default build returns
+ * WD_ERR_INVALID_ARG. */
+int wd_timeline_set(void* blocks, void* phases);
+
 /* Human-readable name of a status code (static string). */
 const char* wd_status_string(int status);
 

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <vector>
+
 #include "handle.h"
 
 namespace wd {
@@ -207,6 +209,18 @@ cudaError_t launch_unitarity(int nlinks, const double* U, unsigned long long* ou
 
 }  // namespace wd
 
+#ifdef WD_TIMELINE
+namespace wd {
+namespace tl {
+static std::vector<int (*)(void*, void*)>& units() {
+    static std::vector<int (*)(void*, void*)> u;
+    return u;
+}
+void register_unit(int (*setter)(void*, void*)) { units().push_back(setter); }
+}  // namespace tl
+}  // namespace wd
+#endif
+
 using namespace wd;
 
 extern "C" {
@@ -319,6 +333,18 @@ int wd_set_arith(wd_handle* h, int bits) {
 }
 
 int wd_get_arith(const wd_handle* h) { return h ? (h->arith16 ? 16 : 32) : 0; }
+
+int wd_timeline_set(void* blocks, void* phases) {
+#ifdef WD_TIMELINE
+    int bad = 0;
+    for (auto f : wd::tl::units()) bad |= f(blocks, phases);
+    return bad ? WD_ERR_CUDA : WD_OK;
+#else
+    (void)blocks;
+    (void)phases;
+    return WD_ERR_INVALID_ARG;
+#endif
+}
 
 int wd_set_wait_limit(wd_handle* h, long long rounds) {
     if (!h) return WD_ERR_INVALID_ARG;

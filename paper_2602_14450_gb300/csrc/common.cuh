@@ -14,6 +14,78 @@
 
 namespace wd {
 
+// ------------------------------------------------------------ timeline ---
+//
+// Timeline build (-DWD_TIMELINE, python -m paper_2602_14450_gb300.timeline):
+// each block of a kernel that opens with pdl_begin() records its kernel site,
+// grid size, SM, arrival, start (after the wait for the preceding kernel) and
+// end on the global timer; the last block of each grid reduction records the
+// times of its phases. The default build contains none of it.
+#ifdef WD_TIMELINE
+namespace tl {
+static __device__ unsigned long long* blocks = nullptr;   // [0] records, then 4 words per block
+static __device__ unsigned long long* phases = nullptr;   // [0] records, then 10 words per reduction
+constexpr unsigned long long BLOCK_CAP = 1ull << 24, PHASE_CAP = 1ull << 20;
+__device__ __forceinline__ unsigned long long now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned sm() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+// 16-bit hash of a source file's base name (the same function in timeline.py)
+__host__ __device__ constexpr unsigned name_hash(const char* c, unsigned h = 7u) {
+    return *c ? name_hash(c + 1, h * 31u + (unsigned char)*c) : (h & 0xFFFFu);
+}
+__host__ __device__ constexpr const char* base_name(const char* p, const char* last) {
+    return *p ? base_name(p + 1, *p == '/' ? p + 1 : last) : last;
+}
+struct Scope {
+    unsigned long long arrive, start;
+    unsigned site;
+    __device__ Scope(unsigned site_, unsigned long long arrive_) : arrive(arrive_), start(now()), site(site_) {}
+    __device__ ~Scope() {
+        if (threadIdx.x != 0 || !blocks) return;
+        const unsigned long long end = now();
+        const unsigned long long r = atomicAdd(blocks, 1ull);
+        if (r >= BLOCK_CAP) return;
+        unsigned long long* q = blocks + 1 + 4 * r;
+        q[0] = ((unsigned long long)site << 32) | ((unsigned long long)gridDim.x << 8) | sm();
+        q[1] = arrive;
+        q[2] = start;
+        q[3] = end;
+    }
+};
+__device__ __forceinline__ void record_phases(int stage, int nsum, const unsigned long long (&t)[8]) {
+    if (!phases) return;
+    const unsigned long long end = now();
+    const unsigned long long r = atomicAdd(phases, 1ull);
+    if (r >= PHASE_CAP) return;
+    unsigned long long* q = phases + 1 + 10 * r;
+    q[0] = ((unsigned long long)stage << 32) | (unsigned)nsum;
+    for (int i = 0; i < 8; ++i) q[1 + i] = t[i];
+    q[9] = end;
+}
+// Points the recording buffers of this translation unit's kernels at b and p.
+static int set_buffers(void* b, void* p) {
+    if (cudaMemcpyToSymbol(blocks, &b, sizeof(b)) != cudaSuccess) return 1;
+    return cudaMemcpyToSymbol(phases, &p, sizeof(p)) != cudaSuccess ? 1 : 0;
+}
+void register_unit(int (*setter)(void*, void*));   // api.cu: the setters of all translation units
+static const int registered = (register_unit(set_buffers), 0);
+}  // namespace tl
+#define WD_TL_DECL unsigned long long wd_tl_t[8] = {};
+#define WD_TL_T(i) wd_tl_t[i] = ::wd::tl::now();
+#define WD_TL_PHASES(stage, nsum) ::wd::tl::record_phases(stage, nsum, wd_tl_t);
+#else
+#define WD_TL_DECL
+#define WD_TL_T(i)
+#define WD_TL_PHASES(stage, nsum)
+#endif
+
 // ---------------------------------------------------------------- storage ---
 
 template <typename T> struct Unit;
@@ -667,21 +739,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
 template <int NSUM, int HINT = ST_NONE>
 __device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const RedCtx& rc, const Slice& sl) {
     __shared__ unsigned is_last;
+    WD_TL_DECL
+    WD_TL_T(0)
     double* part = rc.partials + (size_t)sl.rhs * RED_STRIDE;
     unsigned* ticket = rc.ticket + sl.rhs;
     double v[NSUM];
 #pragma unroll
     for (int k = 0; k < NSUM; ++k) v[k] = vin[k];
     block_sum<NSUM>(v);
+    WD_TL_T(1)
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = v[k];
         __threadfence();
+        WD_TL_T(2)
         is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
+        WD_TL_T(3)
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    WD_TL_T(4)
     double acc[NSUM];
 #pragma unroll
     for (int k = 0; k < NSUM; ++k) acc[k] = 0.0;
@@ -699,11 +777,15 @@ __device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const Red
 #pragma unroll
             for (int k = 0; k < NSUM; ++k) acc[k] += t[i][k];
     }
+    WD_TL_T(5)
     block_sum<NSUM>(acc);
     if (threadIdx.x == 0) {
+        WD_TL_T(6)
         if (rc.st) run_stage_hinted<HINT>(rc.stage, acc, rc.st + sl.rhs);
+        WD_TL_T(7)
         *ticket = 0u;
         __threadfence();
+        WD_TL_PHASES(rc.stage, NSUM)
     }
 }
 
@@ -780,6 +862,8 @@ __device__ __forceinline__ void block_sum(F2 (&v)[NSUM]) {
 template <int NSUM, int HINT = ST_NONE>
 __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCtx& rc, const Slice& sl) {
     __shared__ unsigned is_last;
+    WD_TL_DECL
+    WD_TL_T(0)
     float2* part = reinterpret_cast<float2*>(rc.partials + (size_t)sl.rhs * RED_STRIDE);
     unsigned* ticket = rc.ticket + sl.rhs;
     F2 v[NSUM];
@@ -789,15 +873,19 @@ __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCt
     for (int pass = 0;; ++pass) {
         block_sum<NSUM>(v);
         if (pass == 1) break;
+        WD_TL_T(1)
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = make_float2(v[k].hi, v[k].lo);
             __threadfence();
+            WD_TL_T(2)
             is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
+            WD_TL_T(3)
         }
         __syncthreads();
         if (!is_last) return;
         __threadfence();
+        WD_TL_T(4)
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) v[k] = F2{0.f, 0.f};
 #pragma unroll 3
@@ -808,14 +896,18 @@ __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCt
 #pragma unroll
             for (int k = 0; k < NSUM; ++k) v[k] = f2_add(v[k], F2{t[k].x, t[k].y});
         }
+        WD_TL_T(5)
     }
     if (threadIdx.x == 0) {
+        WD_TL_T(6)
         double a[NSUM];
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) a[k] = (double)v[k].hi + (double)v[k].lo;
         if (rc.st) run_stage_hinted<HINT>(rc.stage, a, rc.st + sl.rhs);
+        WD_TL_T(7)
         *ticket = 0u;
         __threadfence();
+        WD_TL_PHASES(rc.stage, NSUM)
     }
 }
 
@@ -824,10 +916,23 @@ __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCt
 // still running. It first waits for that predecessor to complete and its
 // writes to be visible, then lets its own successor start launching. Both
 // instructions do nothing for a kernel launched the ordinary way.
-__device__ __forceinline__ void pdl_begin() {
+__device__ __forceinline__ void pdl_begin_wait() {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
+// A kernel may declare a local wd_tl_tag (0-15) before pdl_begin() to tell
+// its variants apart in the timeline records (the hops: their reduction).
+constexpr unsigned wd_tl_tag = 0;
+#ifdef WD_TIMELINE
+#define pdl_begin()                                                                                           \
+    const unsigned long long wd_tl_arrive = ::wd::tl::now();                                                  \
+    pdl_begin_wait();                                                                                         \
+    const ::wd::tl::Scope wd_tl_scope((unsigned)__LINE__ | (wd_tl_tag << 12) |                                 \
+                                          (::wd::tl::name_hash(::wd::tl::base_name(__FILE__, __FILE__)) << 16), \
+                                      wd_tl_arrive)
+#else
+#define pdl_begin() pdl_begin_wait()
+#endif
 
 // Guards: inner-loop kernels return once the inner solve of their right-hand
 // side is done (or the right-hand side is finished); refinement kernels only

@@ -173,6 +173,7 @@ template <int R, int RED, bool MAT, int AHEAD = 2> struct Hop16Bounds {
 template <int R, int EPI, int RED, bool MAT, int AHEAD = 2>
 __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT, AHEAD>::THREADS, Hop16Bounds<R, RED, MAT, AHEAD>::MIN_BLOCKS)
     hop16_kernel(const HopParams P) {
+    [[maybe_unused]] constexpr unsigned wd_tl_tag = RED;   // timeline records: the reduction
     pdl_begin();
     typedef LinkFmt<__half, R> LF;
     constexpr int NS = RedSums<RED>::N;

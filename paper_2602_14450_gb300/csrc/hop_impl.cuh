@@ -346,6 +346,7 @@ template <typename T, int RED, bool PF, bool MAT = false> struct HopBounds {
 template <typename T, int R, int EPI, int RED, bool PF, bool PAIR = false, bool MAT = false>
 __global__ void __launch_bounds__(HopBounds<T, RED, PF, MAT>::THREADS, HopBounds<T, RED, PF, MAT>::MIN_BLOCKS)
     hop_kernel(const HopParams P) {
+    [[maybe_unused]] constexpr unsigned wd_tl_tag = RED;   // timeline records: the reduction
     pdl_begin();
     typedef typename Unit<T>::C C;
     typedef LinkFmt<T, R> LF;

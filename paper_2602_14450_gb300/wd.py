@@ -35,7 +35,7 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
            "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit", "wd_apply_batch",
-           "wd_set_rhs_per_thread", "wd_fma_probe"]
+           "wd_set_rhs_per_thread", "wd_fma_probe", "wd_timeline_set"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -71,6 +71,15 @@ class SolveStats(C.Structure):
 _lib = None
 
 
+def use_library(path: str) -> None:
+    """Load the library from `path` instead of libwd.so (before the first call
+    into it; the timeline build, for instance)."""
+    global LIB_PATH
+    if _lib is not None and path != LIB_PATH:
+        raise RuntimeError("the library is already loaded from " + LIB_PATH)
+    LIB_PATH = path
+
+
 def lib():
     """Load libwd.so (raises if it has not been built)."""
     global _lib
@@ -87,6 +96,7 @@ def lib():
         L.wd_set_arith.argtypes = [vp, i]
         L.wd_get_arith.argtypes = [vp]
         L.wd_set_wait_limit.argtypes = [vp, C.c_longlong]
+        L.wd_timeline_set.argtypes = [vp, vp]
         L.wd_vector_bytes.argtypes = [vp, i]
         L.wd_vector_bytes.restype = sz
         L.wd_pack.argtypes = [vp, i, i, vp, vp, vp]
