@@ -731,6 +731,17 @@ __device__ __forceinline__ void block_sum(double (&v)[NSUM]) {
     }
 }
 
+// The ticket of a grid reduction: an add with acquire-release semantics at GPU
+// scope. Its release orders the block's partial-sum stores before it; its
+// acquire, with the barrier that follows, orders the last block's loads of
+// all partial sums (from L2) after every other block's release. The ticket is
+// re-armed with a plain store: the next kernel sees it after this one ends.
+__device__ __forceinline__ unsigned ticket_add(unsigned* t) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(t) : "memory");
+    return old;
+}
+
 // Reduce v over the sl.nb blocks that serve right-hand side sl.rhs (HINT: the
 // scalar stage the calling kernel expects to run). The last block adds the partial sums with all its threads (each thread loads its
 // eight next partials before adding them, so the loads overlap), then sums
@@ -751,14 +762,12 @@ __device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const Red
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = v[k];
-        __threadfence();
         WD_TL_T(2)
-        is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
+        is_last = (ticket_add(ticket) == (unsigned)sl.nb - 1) ? 1u : 0u;
         WD_TL_T(3)
     }
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
     WD_TL_T(4)
     double acc[NSUM];
 #pragma unroll
@@ -784,7 +793,6 @@ __device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const Red
         if (rc.st) run_stage_hinted<HINT>(rc.stage, acc, rc.st + sl.rhs);
         WD_TL_T(7)
         *ticket = 0u;
-        __threadfence();
         WD_TL_PHASES(rc.stage, NSUM)
     }
 }
@@ -877,14 +885,12 @@ __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCt
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int k = 0; k < NSUM; ++k) part[(size_t)sl.b * NSUM + k] = make_float2(v[k].hi, v[k].lo);
-            __threadfence();
             WD_TL_T(2)
-            is_last = (atomicAdd(ticket, 1u) == (unsigned)sl.nb - 1) ? 1u : 0u;
+            is_last = (ticket_add(ticket) == (unsigned)sl.nb - 1) ? 1u : 0u;
             WD_TL_T(3)
         }
         __syncthreads();
         if (!is_last) return;
-        __threadfence();
         WD_TL_T(4)
 #pragma unroll
         for (int k = 0; k < NSUM; ++k) v[k] = F2{0.f, 0.f};
@@ -906,7 +912,6 @@ __device__ __forceinline__ void grid_reduce(const float (&vf)[NSUM], const RedCt
         if (rc.st) run_stage_hinted<HINT>(rc.stage, a, rc.st + sl.rhs);
         WD_TL_T(7)
         *ticket = 0u;
-        __threadfence();
         WD_TL_PHASES(rc.stage, NSUM)
     }
 }
