@@ -530,6 +530,37 @@ __global__ void __launch_bounds__(256) k_norm2(int n, int nrhs, long long vs, co
     grid_reduce<1>(d, rc, sl);
 }
 
+// Eq. 5 and the odd half of the true residual from one odd hop t = H_oe xi_e:
+//   xi_o = eta_o + kappa t,   sum over sites of |eta_o - xi_o + kappa t|^2
+// (the stage as given). The residual's own H_oe xi_e is this t: the same
+// kernel on the same input gives the same bits, so it is not recomputed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_odd_reconstruct(int n, int nrhs, long long vs, double kappa, const uint4* eta,
+                                                         const uint4* t, uint4* xo, RedCtx rc) {
+    typedef typename Unit<T>::C C;
+    const Slice sl = slice_of(nrhs);
+    eta += sl.rhs * vs;
+    t += sl.rhs * vs;
+    xo += sl.rhs * vs;
+    const C k = (C)kappa;
+    C s2 = 0;
+    RHS_LOOP(h, n) {
+        C e[24], tv[24], o[24];
+        load_spinor<T>(eta, n, h, e);
+        load_spinor<T>(t, n, h, tv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) o[i] = fma(k, tv[i], e[i]);
+        store_spinor<T>(xo, n, h, o, false);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            const C r = fma(k, tv[i], e[i] - o[i]);
+            s2 += r * r;
+        }
+    }
+    const C d[1] = {s2};
+    grid_reduce<1>(d, rc, sl);
+}
+
 // lex FP64 (24 doubles per site) -> packed parity vector of T
 template <typename T>
 __global__ void k_pack(Geom g, int parity, const double* lex, uint4* out) {

@@ -77,6 +77,9 @@ template <typename T> struct Ops {
                                const SolverState* st, cudaStream_t s);
     static cudaError_t norm2(int n, int nrhs, long long vs, const uint4* v, RedCtx rc, int guard_kind,
                              cudaStream_t s);
+    // xo = eta + kappa t and the sum of |eta - xo + kappa t|^2 (Eq. 5 with t = H_oe xi_e)
+    static cudaError_t odd_reconstruct(int n, int nrhs, long long vs, double kappa, const uint4* eta, const uint4* t,
+                                       uint4* xo, RedCtx rc, cudaStream_t s);
     // out = M in, site by site, for every right-hand side (M: 12 x 12 complex blocks, storage T)
     static cudaError_t apply_mat(int n, int nrhs, long long vs, const uint4* mat, const uint4* in, uint4* out,
                                  cudaStream_t s);

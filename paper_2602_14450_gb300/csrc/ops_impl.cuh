@@ -341,6 +341,14 @@ cudaError_t Ops<T>::norm2(int n, int nrhs, long long vs, const uint4* v, RedCtx 
 }
 
 template <typename T>
+cudaError_t Ops<T>::odd_reconstruct(int n, int nrhs, long long vs, double kappa, const uint4* eta, const uint4* t,
+                                    uint4* xo, RedCtx rc, cudaStream_t s) {
+    const int nb = reduce_blocks((const void*)k_odd_reconstruct<T>, n, VEC_BLOCK, nrhs);
+    k_odd_reconstruct<T><<<nb * nrhs, VEC_BLOCK, 0, s>>>(n, nrhs, vs, kappa, eta, t, xo, rc);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Ops<T>::pack(const Geom& g, int parity, const double* lex, uint4* out, cudaStream_t s) {
     k_pack<T><<<stream_blocks(g.Vh, VEC_BLOCK), VEC_BLOCK, 0, s>>>(g, parity, lex, out);
     return cudaGetLastError();

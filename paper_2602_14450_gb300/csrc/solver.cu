@@ -570,12 +570,12 @@ int solve_systems(int n, wd_handle* const* hs, const int* nrhs, const double* co
             WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.tmp64, -1.0, ST_ACC,
                              GUARD_NONE, s));
             nk += 3;
-        } else {
-            WD_CUDA(h, hop64(S, 1, S.x64, S.xo, EPI_Y, RED_NONE, kap, S.eta_o, 1.0, nullptr, 0.0, ST_NONE, GUARD_NONE,
-                             s));
-            WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.x64, -1.0, ST_ACC_SET,
+        } else {   // t = H_oe xi_e; xi_o = eta_o + kappa t, |r_o|^2; r_e = eta_e - xi_e + kappa H_eo xi_o, |r_e|^2
+            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_H, RED_NONE, 1.0, nullptr, 0.0, nullptr, 0.0, ST_NONE,
                              GUARD_NONE, s));
-            WD_CUDA(h, hop64(S, 1, S.x64, S.tmp64, EPI_YZ, RED_NORM, kap, S.eta_o, 1.0, S.xo, -1.0, ST_ACC,
+            WD_CUDA(h, Ops<double>::odd_reconstruct(h->g.Vh, S.nrhs, S.vs64, kap, S.eta_o, S.tmp64, S.xo,
+                                                    red_ctx(h, ST_ACC_SET), s));
+            WD_CUDA(h, hop64(S, 0, S.xo, S.r64, EPI_YZ, RED_NORM, kap, S.eta_e, 1.0, S.x64, -1.0, ST_ACC,
                              GUARD_NONE, s));
         }
         for (int r = 0; r < S.nrhs; ++r) {

@@ -31,8 +31,8 @@ from . import build as B
 STAGES = {1: "init", 2: "alpha", 3: "omega", 4: "rnorm", 5: "end", 6: "outer", 7: "acc", 8: "acc_set",
           9: "end (fused rescaling)"}
 TAGS = {1: "(r*,v)", 2: "(t,s)", 3: "norm"}   # the reduction a hop's records are tagged with
-PHASES = ["block sum", "partials out + fence", "ticket", "sync + fence", "partials summed", "block sum 2",
-          "scalar stage", "reset + fence"]
+PHASES = ["block sum", "partials out", "ticket", "barrier", "partials summed", "block sum 2", "scalar stage",
+          "ticket re-armed"]
 
 
 def name_hash(s: str) -> int:
