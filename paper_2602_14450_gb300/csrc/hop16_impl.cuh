@@ -160,6 +160,101 @@ __device__ __forceinline__ void reconstruct16(int mu, bool fwd, unsigned fb, con
     }
 }
 
+// Epilogue of the FP16-arithmetic hop with Blackwell's packed FP32x2
+// multiply and FMA (one complex number per float2): the half2 accumulator is
+// widened and unscaled pairwise and out = a H + b y (+ c z) is formed with the
+// same per-lane roundings as the scalar epilogue, then rounded to FP16 and
+// stored. The dot products of the stored values are the scalar epilogue's
+// expressions term for term, so every result has the scalar epilogue's bits.
+template <int EPI, int RED>
+__device__ __forceinline__ void epilogue16x2(const HopParams& P, uint4* vout, const uint4* vy, const uint4* vz,
+                                             const uint4* vrs, int h, const __half2 (&acc)[12], float unscale,
+                                             float (&part)[RedSums<RED>::N], bool ftz) {
+    const int Vh = P.g.Vh;
+    const float2 us = make_float2(unscale, unscale);
+    const float ca = (float)P.a, cb = (float)P.b, cc = (float)P.c;
+    const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), cc2 = make_float2(cc, cc);
+    float2 o[12];
+    float2 y2[12];
+    if constexpr (EPI >= EPI_Y) {   // o = a H + b y, the product a H fused: fma(a, H, b y)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const uint4 w = __ldg(vy + (size_t)u * Vh + h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = 4 * u + k;
+                y2[i] = __half22float2(as_h2(word_of(w, k)));
+                o[i] = __ffma2_rn(ca2, __fmul2_rn(__half22float2(acc[i]), us), __fmul2_rn(cb2, y2[i]));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float2 a = __fmul2_rn(__half22float2(acc[i]), us);
+            o[i] = (EPI == EPI_H && P.a == 1.0) ? a : __fmul2_rn(ca2, a);
+        }
+    }
+    if constexpr (EPI >= EPI_YZ) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const uint4 w = __ldg(vz + (size_t)u * Vh + h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[4 * u + k] = __ffma2_rn(cc2, __half22float2(as_h2(word_of(w, k))), o[4 * u + k]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {   // round to FP16, store, and keep the stored values for the dots
+        uint4 w = make_uint4(as_w(__float22half2_rn(o[4 * u])), as_w(__float22half2_rn(o[4 * u + 1])),
+                             as_w(__float22half2_rn(o[4 * u + 2])), as_w(__float22half2_rn(o[4 * u + 3])));
+        if (ftz) w = Unit<__half>::flush(w);
+        vout[(size_t)u * Vh + h] = w;
+        if constexpr (RED != RED_NONE) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[4 * u + k] = __half22float2(as_h2(word_of(w, k)));
+        }
+    }
+    if constexpr (RED == RED_RSV) {   // conj(r*) o
+        float2 rs[12];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const uint4 w = __ldg(vrs + (size_t)u * Vh + h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rs[4 * u + k] = __half22float2(as_h2(word_of(w, k)));
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            part[0] += rs[i].x * o[i].x + rs[i].y * o[i].y;
+            part[1] += rs[i].x * o[i].y - rs[i].y * o[i].x;
+        }
+    } else if constexpr (RED == RED_TS) {   // (o, q), (o, o), (q, q); q = r* if given, else y
+        float2 q2[12];
+        if (vrs) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const uint4 w = __ldg(vrs + (size_t)u * Vh + h);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q2[4 * u + k] = __half22float2(as_h2(word_of(w, k)));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) q2[i] = y2[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            part[0] += o[i].x * q2[i].x + o[i].y * q2[i].y;
+            part[1] += o[i].x * q2[i].y - o[i].y * q2[i].x;
+            part[2] += o[i].x * o[i].x + o[i].y * o[i].y;
+            part[3] += q2[i].x * q2[i].x + q2[i].y * q2[i].y;
+        }
+    } else if constexpr (RED == RED_NORM) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            part[0] += o[i].x * o[i].x;
+            part[0] += o[i].y * o[i].y;
+        }
+    }
+}
+
 // Launch shape: one site per thread, 128 threads; the plain hop fits 64
 // registers with 12-real links (8 blocks per SM) and 72 with 18-real links;
 // loading the neighbour spinors two directions ahead (AHEAD = 2) takes 72.
@@ -254,7 +349,7 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT, AHEAD>::THREADS, Hop1
                 if (ftz) w = Unit<__half>::flush(w);
                 vout[(size_t)u * Vh + h] = w;
             }
-        } else {
+        } else if constexpr (MAT) {
             float a32[24];
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
@@ -262,6 +357,8 @@ __global__ void __launch_bounds__(Hop16Bounds<R, RED, MAT, AHEAD>::THREADS, Hop1
                 a32[2 * i + 1] = __high2float(acc[i]) * unscale;
             }
             hop_epilogue<__half, EPI, RED, MAT>(P, vout, vy, vz, vrs, h, a32, part, ftz);
+        } else {
+            epilogue16x2<EPI, RED>(P, vout, vy, vz, vrs, h, acc, unscale, part, ftz);
         }
     }
 
