@@ -808,25 +808,43 @@ __device__ __forceinline__ void grid_reduce(const double (&vin)[NSUM], const Red
 struct F2 {
     float hi, lo;
 };
+// Round-to-nearest FP32 add and subtract, never contracted or reassociated
+// (host versions for the host-side tests of these sums).
+__host__ __device__ __forceinline__ float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    volatile float s = a + b;
+    return s;
+#endif
+}
+__host__ __device__ __forceinline__ float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    volatile float s = a - b;
+    return s;
+#endif
+}
 // TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e == a + b exactly in round-to-nearest.
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+__host__ __device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = add_rn(a, b);
+    const float bb = sub_rn(s, a);
+    const float e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
     return {s, e};
 }
 // Fast2Sum (Dekker 1971): exact when |a| >= |b|.
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+__host__ __device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+    const float s = add_rn(a, b);
+    return {s, sub_rn(b, sub_rn(s, a))};
 }
 // x + y: the accurate double-word addition (sums of the high and of the low
 // words by TwoSum, each followed by a renormalisation; Hida, Li and Bailey 2001).
-__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+__host__ __device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
     F2 s = two_sum(x.hi, y.hi);
     const F2 t = two_sum(x.lo, y.lo);
-    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+    s = fast_two_sum(s.hi, add_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, add_rn(s.lo, t.lo));
 }
 
 template <int NSUM>
