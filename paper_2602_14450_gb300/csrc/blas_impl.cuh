@@ -5,6 +5,8 @@
 // paper's Fig. 3) and combine threads, blocks and the grid in FP64.
 #pragma once
 
+#include <cstring>
+
 #include "kernels.h"
 
 namespace wd {
@@ -295,13 +297,61 @@ __global__ void __launch_bounds__(256) k_scale(int n, int nrhs, long long vs, ui
 
 // Rescale the FP64 outer residual and demote it (Alg. 3, first lines):
 // y~ = low_prec((s / |r|) r) written to r and r*; sums |single(y~)|^2 and the
-// count of nonzero reals. The product is formed in FP64 and rounded once.
+// count of nonzero reals. The product is formed in FP64 and rounded once (round_f64).
+// Round-to-nearest-even of an FP64 value to a binary format with MB fraction
+// bits and EB exponent bits, from the IEEE-754 bit fields in integer
+// arithmetic (the FP64 pipe of this GPU is ~70x narrower than the integer
+// one): the fraction is cut after MB bits and rounded on the dropped bits (a
+// carry into the exponent field is the correct result, up to infinity);
+// below the normal range the significand is shifted to units of the smallest
+// subnormal and rounded the same way; beyond it the result is infinity;
+// infinities stay, NaNs become quiet NaNs. Returns the bit pattern.
+template <int MB, int EB>
+__host__ __device__ __forceinline__ unsigned round_f64(double x) {
+    constexpr int BIAS = (1 << (EB - 1)) - 1, EMIN = 1 - BIAS;
+    constexpr unsigned EXP_ALL = (1u << EB) - 1u;
+#ifdef __CUDA_ARCH__
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long u;
+    memcpy(&u, &x, sizeof u);
+#endif
+    const unsigned sign = (unsigned)(u >> 63) << (EB + MB);
+    const int e = (int)((u >> 52) & 0x7FF);
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return sign | (EXP_ALL << MB) | (m ? (1u << (MB - 1)) : 0u);
+    const int E = e - 1023;
+    if (E > BIAS) return sign | (EXP_ALL << MB);
+    unsigned long long q, r, half;
+    unsigned v;
+    if (E >= EMIN) {
+        q = m >> (52 - MB);
+        r = m & ((1ull << (52 - MB)) - 1);
+        half = 1ull << (51 - MB);
+        v = sign | ((unsigned)(E + BIAS) << MB) | (unsigned)q;
+    } else {
+        const int sh = 52 + EMIN - MB - E;   // value / (smallest subnormal) = significand >> sh
+        if (sh > 53) return sign;             // below half the smallest subnormal
+        const unsigned long long mf = (1ull << 52) | m;
+        q = mf >> sh;
+        r = mf & ((1ull << sh) - 1);
+        half = 1ull << (sh - 1);
+        v = sign | (unsigned)q;
+    }
+    if (r > half || (r == half && (q & 1ull))) v += 1u;
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
-template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
-template <> __device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return __uint_as_float(round_f64<23, 8>(v)); }
+template <> __device__ __forceinline__ __half from_double<__half>(double v) {
+    return __ushort_as_half((unsigned short)round_f64<10, 5>(v));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
+    return __ushort_as_bfloat16((unsigned short)round_f64<7, 8>(v));
+}
 
 // Exact widening of a storage value to the arithmetic type C of its unit.
 template <typename T>
