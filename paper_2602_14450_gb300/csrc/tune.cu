@@ -99,7 +99,6 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
     const int ri = recon == 12 ? 0 : 1;
     int best_k[2] = {1, 1}, best_lsm[2] = {0, 0}, best_spt = 1;
     float best16[2] = {1e30f, 1e30f};
-    float plain_spt_ms[3] = {1e30f, 1e30f, 1e30f};   // the plain hop, one right-hand side per thread: 1, 2, 4 sites
     int cands16 = 0;
     if (prec == WD_FP16 && h->arith16 && err == cudaSuccess) {
         P.arith16 = 1;
@@ -130,7 +129,6 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
                     if (err != cudaSuccess) break;
                     ms /= 8.f;
                     if (form == 0) ++cands16;
-                    if (form == 0 && k == 1) plain_spt_ms[shape] = ms;
                     if (ms < best16[form]) {
                         best16[form] = ms;
                         best_k[form] = k;
@@ -140,18 +138,6 @@ extern "C" int wd_tune(wd_handle* h, int prec, int recon, int nrhs, void* stream
                 }
             }
         }
-    }
-    // Sites per thread of the plain hop: the largest count within 2% of the fastest. Timed in isolation the
-    // shapes come within ~1% of each other at 32^3 x 64, but inside the solve, where the hop follows a
-    // streaming kernel, two sites per thread ran ~5% faster than one in every measured solve.
-    if (prec == WD_FP16 && h->arith16 && err == cudaSuccess && best_k[0] == 1) {
-        float fastest = 1e30f;
-        for (int i = 0; i < 3; ++i) fastest = plain_spt_ms[i] < fastest ? plain_spt_ms[i] : fastest;
-        for (int i = 0; i < 3; ++i)
-            if (plain_spt_ms[i] <= 1.02f * fastest) {
-                best_spt = 1 << i;
-                best16[0] = plain_spt_ms[i];
-            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
