@@ -116,6 +116,8 @@ def main():
     rec = blocks[1: 1 + 4 * min(nb, 1 << 24)].view(-1, 4).cpu().numpy().astype(np.int64)
     ph = phases[1: 1 + 10 * min(nph, 1 << 20)].view(-1, 10).cpu().numpy().astype(np.int64)
 
+    if nb == 0:
+        raise RuntimeError("no kernel blocks were recorded (is libwd_timeline.so the library in use?)")
     sites = kernel_sites()
     ls = launches_of(rec)
     span = (ls[-1]["end"] - ls[0]["start"]) / 1e3
