@@ -472,7 +472,7 @@ enum Stage {
 // Status codes (mirror enum wd_status of wd.h).
 enum { S_OK = 0, S_NOT_CONVERGED = 4, S_BREAKDOWN = 5, S_NONFINITE = 6 };
 
-__device__ __forceinline__ void stop(SolverState* st, int status) {
+__host__ __device__ __forceinline__ void stop(SolverState* st, int status) {
     st->done = 1;
     if (st->status == S_OK) st->status = status;
 }
@@ -484,9 +484,18 @@ __device__ __forceinline__ void stop(SolverState* st, int status) {
 // round trip to memory), divides once where a reciprocal serves several
 // products, and stores only what it changes.
 
+// 1 / sqrt(x): the device's reciprocal square root, the plain quotient in host builds of these stages.
+__host__ __device__ __forceinline__ double rsqrt_d(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
 // End of a BiCGStab iteration (Alg. 4 last lines): gamma known, r stored.
 // rn2 = |r_stored|^2, rs = (r*, r_stored).
-__device__ __forceinline__ void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
+__host__ __device__ __forceinline__ void end_iteration(SolverState* st, double gamma, double rn2, const double* rs) {
     const double rho0 = st->rho[0], rho1 = st->rho[1];
     const double al0 = st->alpha[0], al1 = st->alpha[1], om0 = st->omega[0], om1 = st->omega[1];
     const double gp = st->gamma_p * gamma;
@@ -540,9 +549,9 @@ __device__ __forceinline__ void end_iteration(SolverState* st, double gamma, dou
 // function per stage; a kernel inlines the stage it expects (its code then
 // follows the final sum in instruction memory) and calls the shared
 // out-of-line dispatcher for any other.
-template <int STAGE> __device__ __forceinline__ void stage_fn(const double* s, SolverState* st) {}
+template <int STAGE> __host__ __device__ __forceinline__ void stage_fn(const double* s, SolverState* st) {}
 
-template <> __device__ __forceinline__ void stage_fn<ST_INIT>(const double* s, SolverState* st) {
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_INIT>(const double* s, SolverState* st) {
     double n2 = s[0];
     st->shat = sqrt(n2);
     st->nonzeros = (long long)s[1];
@@ -565,7 +574,7 @@ template <> __device__ __forceinline__ void stage_fn<ST_INIT>(const double* s, S
     if (!(n2 > 0) || !isfinite(n2)) stop(st, isfinite(n2) ? S_OK : S_NONFINITE);
 }
 
-template <> __device__ __forceinline__ void stage_fn<ST_ALPHA>(const double* s, SolverState* st) {   // alpha = rho / (r*, v)
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_ALPHA>(const double* s, SolverState* st) {   // alpha = rho / (r*, v)
     const double rho0 = st->rho[0], rho1 = st->rho[1];
     const double v0 = s[0], v1 = s[1];
     if (!(isfinite(v0) && isfinite(v1))) { stop(st, S_NONFINITE); return; }
@@ -576,7 +585,7 @@ template <> __device__ __forceinline__ void stage_fn<ST_ALPHA>(const double* s, 
 }
 
 // omega = (t, s) / (t, t) with the omega_0 prescription; with fused rescaling also the factor for r
-template <> __device__ __forceinline__ void stage_fn<ST_OMEGA>(const double* s, SolverState* st) {
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_OMEGA>(const double* s, SolverState* st) {
     const double omega0 = st->omega0, sigma = st->sigma;
     const double c = st->lambda_p / st->gamma_p;
     const double al0 = st->alpha[0], al1 = st->alpha[1];
@@ -598,7 +607,7 @@ template <> __device__ __forceinline__ void stage_fn<ST_OMEGA>(const double* s, 
         // cancellation; the factor sigma / g~ rescales r as it is stored
         double r2 = ss - 2.0 * (om0 * ts0 + om1 * ts1) + (om0 * om0 + om1 * om1) * tt;
         r2 = fmax(r2, 1e-12 * ss);
-        const double gt = sigma * rsqrt(r2);
+        const double gt = sigma * rsqrt_d(r2);
         st->gam_tmp = gt;
         if (!isfinite(gt)) { stop(st, S_NONFINITE); return; }
     }
@@ -608,7 +617,7 @@ template <> __device__ __forceinline__ void stage_fn<ST_OMEGA>(const double* s, 
     st->cXp[1] = c * al1;
 }
 
-template <> __device__ __forceinline__ void stage_fn<ST_RNORM>(const double* s, SolverState* st) {
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_RNORM>(const double* s, SolverState* st) {
     double r2 = s[0], x2 = s[1];
     double rs[2] = {s[2], s[3]};
     st->g = sqrt(r2);
@@ -621,14 +630,14 @@ template <> __device__ __forceinline__ void stage_fn<ST_RNORM>(const double* s, 
     }
 }
 
-template <> __device__ __forceinline__ void stage_fn<ST_END>(const double* s, SolverState* st) {
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_END>(const double* s, SolverState* st) {
     double rn2 = s[0];
     double rs[2] = {s[1], s[2]};
     double gamma = st->sigma > 0.0 ? (st->recalc ? sqrt(rn2) / st->g : st->gam_tmp) : 1.0;
     end_iteration(st, gamma, rn2, rs);
 }
 
-template <> __device__ __forceinline__ void stage_fn<ST_RFUSED>(const double* s, SolverState* st) {
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_RFUSED>(const double* s, SolverState* st) {
     const int recalc = st->recalc;
     const double gt = st->gam_tmp;
     const double r2 = s[0], rn2 = s[1];
@@ -640,13 +649,13 @@ template <> __device__ __forceinline__ void stage_fn<ST_RFUSED>(const double* s,
     end_iteration(st, gamma, rn2, rs);
 }
 
-template <> __device__ __forceinline__ void stage_fn<ST_OUTER>(const double* s, SolverState* st) { st->rnorm = sqrt(s[0]); }
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_OUTER>(const double* s, SolverState* st) { st->rnorm = sqrt(s[0]); }
 
-template <> __device__ __forceinline__ void stage_fn<ST_ACC>(const double* s, SolverState* st) { st->acc += s[0]; }
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_ACC>(const double* s, SolverState* st) { st->acc += s[0]; }
 
-template <> __device__ __forceinline__ void stage_fn<ST_ACC_SET>(const double* s, SolverState* st) { st->acc = s[0]; }
+template <> __host__ __device__ __forceinline__ void stage_fn<ST_ACC_SET>(const double* s, SolverState* st) { st->acc = s[0]; }
 
-static __device__ __noinline__ void run_stage(int stage, const double* s, SolverState* st) {
+static __host__ __device__ __noinline__ void run_stage(int stage, const double* s, SolverState* st) {
     switch (stage) {
     case ST_INIT: stage_fn<ST_INIT>(s, st); break;
     case ST_ALPHA: stage_fn<ST_ALPHA>(s, st); break;
