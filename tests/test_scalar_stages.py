@@ -1,6 +1,7 @@
 """The FP64 scalar recurrence of the inner BiCGStab (Alg. 4) as the reducing
 kernels run it (csrc/common.cuh: run_stage, the alpha, omega and end-of-
-iteration stages), compiled for the host and compared with the recurrence
+iteration stages, and the norm and rescale-pass stages of Alg. 5), compiled
+for the host and compared with the recurrence
 written out from its definitions:
 
   alpha = rho / (r*, v);
@@ -9,8 +10,13 @@ written out from its definitions:
   with the rescaling of r fused: |s - omega t|^2 from the three sums, floored at
   1e-12 (s, s), and the factor sigma / sqrt of it; x-update coefficients
   (lambda'/gamma') omega and (lambda'/gamma') alpha;
+  after the x/r update without fused rescaling: g = |r|, lambda =
+  sigma_lambda / |x| (Alg. 5), then the rescale pass's factor sigma / g or the
+  end of the iteration with gamma = 1; after the rescale pass: gamma from its
+  sums and the earlier g;
   end of iteration: g = |r|, gamma = |r_stored| / g (recalculated) or the
-  factor applied, rho' = gamma rho, gamma' *= gamma, alpha' = alpha,
+  factor applied, rho' = gamma rho, gamma' *= gamma, lambda' *= lambda
+  (Alg. 5), alpha' = alpha,
   omega' = omega, rho = (r*, r_stored), beta = rho alpha' / (rho' omega'),
   p-update coefficients gamma beta and gamma beta omega', |r| / gamma' as the
   residual, and the stopping tests (non-finite, converged, matvec cap,
@@ -41,8 +47,8 @@ void wd::tl::register_unit(int (*)(void*, void*)) {}
 int main() {
     int stage;
     while (std::scanf("%d", &stage) == 1) {
-        double s[4], d[14];
-        int iv[7];
+        double s[4], d[16];
+        int iv[8];
         for (double& v : s) std::scanf("%la", &v);
         for (double& v : d) std::scanf("%la", &v);
         for (int& v : iv) std::scanf("%d", &v);
@@ -50,13 +56,15 @@ int main() {
         st.rho[0] = d[0]; st.rho[1] = d[1]; st.alpha[0] = d[2]; st.alpha[1] = d[3];
         st.omega[0] = d[4]; st.omega[1] = d[5]; st.gamma_p = d[6]; st.lambda_p = d[7]; st.lam = d[8];
         st.sigma = d[9]; st.omega0 = d[10]; st.eps = d[11]; st.bnorm = d[12]; st.gam_tmp = d[13];
+        st.g = d[14]; st.sigma_lambda = d[15];
         st.recalc = iv[0]; st.rescale_x = iv[1]; st.fused_scale = iv[2]; st.iter = iv[3]; st.matvecs = iv[4];
-        st.max_matvecs = iv[5]; st.status = iv[6];
+        st.max_matvecs = iv[5]; st.status = iv[6]; st.scale_pass = iv[7];
         wd::run_stage(stage, s, &st);
         const double out[] = {st.alpha[0], st.alpha[1], st.omega[0], st.omega[1], st.gam_tmp, st.cXr[0],
                               st.cXr[1], st.cXp[0], st.cXp[1], st.rho_p[0], st.rho_p[1], st.gamma_p,
                               st.alpha_p[0], st.alpha_p[1], st.omega_p[0], st.omega_p[1], st.lambda_p,
-                              st.rho[0], st.rho[1], st.cP[0], st.cP[1], st.cV[0], st.cV[1], st.res, st.g};
+                              st.rho[0], st.rho[1], st.cP[0], st.cP[1], st.cV[0], st.cV[1], st.res, st.g,
+                              st.lam};
         for (double v : out) std::printf("%a ", v);
         std::printf("%d %d %d %d\n", st.iter, st.matvecs, st.done, st.status);
     }
@@ -65,8 +73,8 @@ int main() {
 '''
 NAMES = ["alpha0", "alpha1", "omega0", "omega1", "gam_tmp", "cXr0", "cXr1", "cXp0", "cXp1", "rho_p0", "rho_p1",
          "gamma_p", "alpha_p0", "alpha_p1", "omega_p0", "omega_p1", "lambda_p", "rho0", "rho1", "cP0", "cP1", "cV0",
-         "cV1", "res", "g"]
-ST_ALPHA, ST_OMEGA, ST_RFUSED = 2, 3, 9
+         "cV1", "res", "g", "lam"]
+ST_ALPHA, ST_OMEGA, ST_RNORM, ST_END, ST_RFUSED = 2, 3, 4, 5, 9
 S_OK, S_NOT_CONVERGED, S_BREAKDOWN, S_NONFINITE = 0, 4, 5, 6
 
 
@@ -88,7 +96,7 @@ def state(rng, **kw):
           "lambda_p": float(rng.uniform(0.5, 2)), "lam": 1.0, "sigma": 64.0, "omega0": 0.7, "eps": 1e-2,
           "bnorm": 128.0, "gam_tmp": float(rng.uniform(0.5, 2)), "recalc": 1, "rescale_x": 0, "fused_scale": 1,
           "iter": int(rng.integers(0, 100)), "matvecs": int(rng.integers(0, 200)), "max_matvecs": 5000,
-          "status": S_OK}
+          "status": S_OK, "g": float(rng.uniform(0.5, 50)), "sigma_lambda": 256.0, "scale_pass": 0}
     st.update(kw)
     return st
 
@@ -98,9 +106,9 @@ def run(exe, cases):
     for stage, s, st in cases:
         d = [st["rho"].real, st["rho"].imag, st["alpha"].real, st["alpha"].imag, st["omega"].real, st["omega"].imag,
              st["gamma_p"], st["lambda_p"], st["lam"], st["sigma"], st["omega0"], st["eps"], st["bnorm"],
-             st["gam_tmp"]]
+             st["gam_tmp"], st["g"], st["sigma_lambda"]]
         iv = [st["recalc"], st["rescale_x"], st["fused_scale"], st["iter"], st["matvecs"], st["max_matvecs"],
-              st["status"]]
+              st["status"], st["scale_pass"]]
         lines.append(" ".join([str(stage)] + [float(v).hex() for v in list(s) + d] + [str(v) for v in iv]))
     out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
     res = []
@@ -147,9 +155,16 @@ def ref_omega(s, st):
 
 
 def ref_end(s, st):
+    """The fused form: sums |r|^2, |r_stored|^2, (r*, r_stored)."""
     r2, rn2, rs = s[0], s[1], complex(s[2], s[3])
     g = math.sqrt(r2)
     gamma = (math.sqrt(rn2) / g if st["recalc"] else st["gam_tmp"]) if r2 != 0 else 1.0
+    out = ref_end_iteration(st, gamma, rn2, rs, st["lam"])
+    out["g"] = g
+    return out
+
+
+def ref_end_iteration(st, gamma, rn2, rs, lam):
     rho_p = gamma * st["rho"]
     gp = st["gamma_p"] * gamma
     beta = rs * st["alpha"] / (rho_p * st["omega"])
@@ -157,7 +172,8 @@ def ref_end(s, st):
     cv = cp * st["omega"]
     res = math.sqrt(rn2) / gp
     mv = st["matvecs"] + 2
-    out = {"g": g, "rho_p0": rho_p.real, "rho_p1": rho_p.imag, "gamma_p": gp, "alpha_p0": st["alpha"].real,
+    out = {"rho_p0": rho_p.real, "rho_p1": rho_p.imag, "gamma_p": gp, "alpha_p0": st["alpha"].real,
+           "lambda_p": st["lambda_p"] * lam if st["rescale_x"] else st["lambda_p"],
            "alpha_p1": st["alpha"].imag, "omega_p0": st["omega"].real, "omega_p1": st["omega"].imag,
            "rho0": rs.real, "rho1": rs.imag, "cP0": cp.real, "cP1": cp.imag, "cV0": cv.real, "cV1": cv.imag,
            "res": res, "iter": st["iter"] + 1, "matvecs": mv}
@@ -218,3 +234,48 @@ def test_end_of_iteration_stage(stage_exe):
     cases.append((ST_RFUSED, [0.0, 0.0, 0.0, 0.0], state(rng)))   # r = 0 exactly: gamma = 1, converged
     for (stage, s, st), got in zip(cases, run(stage_exe, cases)):
         check(got, ref_end(s, st), (s, st))
+
+
+def ref_rnorm(s, st):
+    """Norms after the x/r update without fused rescaling: |r|^2, |x|^2, (r*, r); then either the rescale pass's
+    factor (Alg. 5 with its separate pass) or the end of the iteration with gamma = 1."""
+    r2, x2, rs = s[0], s[1], complex(s[2], s[3])
+    g = math.sqrt(r2)
+    lam = st["sigma_lambda"] / math.sqrt(x2) if st["rescale_x"] else st["lam"]
+    if st["scale_pass"]:
+        gt = st["sigma"] / g if st["sigma"] > 0 else 1.0
+        out = {"g": g, "gam_tmp": gt, "lam": lam, "done": 0}
+        if not math.isfinite(gt) or (st["rescale_x"] and not math.isfinite(lam)):
+            out.update(done=1, status=S_NONFINITE)
+        return out
+    out = ref_end_iteration(st, 1.0, r2, rs, lam)
+    out.update(g=g, lam=lam)
+    return out
+
+
+def ref_end_after_scale(s, st):
+    """After the rescale pass (Alg. 5): |r_stored|^2, (r*, r_stored); gamma from the g of the norms' stage."""
+    rn2, rs = s[0], complex(s[1], s[2])
+    gamma = (math.sqrt(rn2) / st["g"] if st["recalc"] else st["gam_tmp"]) if st["sigma"] > 0 else 1.0
+    return ref_end_iteration(st, gamma, rn2, rs, st["lam"])
+
+
+def test_norm_and_rescale_pass_stages(stage_exe):
+    rng = np.random.default_rng(34)
+    cases = []
+    for i in range(400):
+        r2, x2 = float(rng.uniform(1e-4, 1e6)), float(rng.uniform(1e-4, 1e6))
+        rs = complex(*rng.standard_normal(2))
+        kw = {"rescale_x": int(i % 2), "scale_pass": int((i // 2) % 2), "lam": float(rng.uniform(0.5, 2)),
+              "sigma": [64.0, 0.0][i % 5 == 0]}
+        cases.append((ST_RNORM, [r2, x2, rs.real, rs.imag], state(rng, **kw)))
+    for i in range(400):
+        rn2 = float(rng.uniform(1e-4, 1e6))
+        rs = complex(*rng.standard_normal(2))
+        kw = {"rescale_x": int(i % 2), "recalc": int((i // 2) % 2), "lam": float(rng.uniform(0.5, 2)),
+              "sigma": [64.0, 0.0][i % 5 == 0]}
+        if i % 7 == 0:
+            kw.update(eps=1e9)
+        cases.append((ST_END, [rn2, rs.real, rs.imag, 0.0], state(rng, **kw)))
+    for (stage, s, st), got in zip(cases, run(stage_exe, cases)):
+        check(got, ref_rnorm(s, st) if stage == ST_RNORM else ref_end_after_scale(s, st), (stage, s, st))
