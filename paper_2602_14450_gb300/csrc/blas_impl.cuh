@@ -366,19 +366,42 @@ template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 
 // sign kept, exponent rebased from 127 to 1023, mantissa shifted into the top
 // of the 52-bit field; float subnormals are normalised, infinities and NaNs
 // keep the all-ones exponent.
-__device__ __forceinline__ double f32_to_f64(float a) {
+__host__ __device__ __forceinline__ double f32_to_f64(float a) {
+#ifdef __CUDA_ARCH__
     const unsigned u = __float_as_uint(a);
+#else
+    unsigned u;
+    memcpy(&u, &a, sizeof u);
+#endif
     const unsigned sgn = u & 0x80000000u;
     unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-    if (e == 0u) {
-        if (m == 0u) return __hiloint2double((int)sgn, 0);
-        const int p = 31 - __clz((int)m);   // leading bit of the subnormal: value = m 2^-149
-        m = (m << (23 - p)) & 0x7FFFFFu;
-        e = (unsigned)(p - 149 + 1023);
+    unsigned hi, lo;
+    if (e == 0u && m == 0u) {
+        hi = sgn;
+        lo = 0u;
     } else {
-        e = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+        if (e == 0u) {   // subnormal: value = m 2^-149, normalised on its leading bit p
+#ifdef __CUDA_ARCH__
+            const int p = 31 - __clz((int)m);
+#else
+            const int p = 31 - __builtin_clz(m);
+#endif
+            m = (m << (23 - p)) & 0x7FFFFFu;
+            e = (unsigned)(p - 149 + 1023);
+        } else {
+            e = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+        }
+        hi = sgn | (e << 20) | (m >> 3);
+        lo = m << 29;
     }
-    return __hiloint2double((int)(sgn | (e << 20) | (m >> 3)), (int)(m << 29));
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((int)hi, (int)lo);
+#else
+    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+#endif
 }
 
 template <typename T>

@@ -50,7 +50,8 @@ int main(int argc, char** argv) {
 def pair_sum_exe():
     d = tempfile.mkdtemp()
     cu, exe = os.path.join(d, "pairs.cu"), os.path.join(d, "pairs")
-    open(cu, "w").write(SRC)
+    with open(cu, "w") as f:
+        f.write(SRC)
     r = subprocess.run([B.nvcc(), *B.ARCH, *B.FLAGS, "-DWD_TIMELINE", "-I", B.CSRC, cu, "-o", exe],
                        capture_output=True, text=True)
     if r.returncode != 0:

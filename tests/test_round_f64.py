@@ -36,7 +36,8 @@ int main() {
 def round_exe():
     d = tempfile.mkdtemp()
     cu, exe = os.path.join(d, "r.cu"), os.path.join(d, "r")
-    open(cu, "w").write(SRC)
+    with open(cu, "w") as f:
+        f.write(SRC)
     r = subprocess.run([B.nvcc(), *B.ARCH, *B.FLAGS, "-DWD_TIMELINE", "-I", B.CSRC, cu, "-o", exe],
                        capture_output=True, text=True)
     if r.returncode != 0:
@@ -78,3 +79,52 @@ def test_round_f64_is_ieee_round_to_nearest_even(round_exe):
     assert np.array_equal(got[~nan, 0], want16[~nan])
     assert np.array_equal(got[~nan, 1], bf[~nan].astype(np.uint64))
     assert np.array_equal(got[~nan, 2], want32[~nan])
+
+
+SRC_WIDEN = r'''
+#include "blas_impl.cuh"
+#include <cstdio>
+void wd::tl::register_unit(int (*)(void*, void*)) {}
+int main() {
+    unsigned bits;
+    while (std::scanf("%x", &bits) == 1) {
+        float f;
+        memcpy(&f, &bits, sizeof f);
+        const double d = wd::f32_to_f64(f);
+        unsigned long long o;
+        memcpy(&o, &d, sizeof o);
+        std::printf("%llx\n", o);
+    }
+    return 0;
+}
+'''
+
+
+def test_f32_to_f64_is_the_exact_widening():
+    """f32_to_f64 (the integer-pipe widening of k_correct and k_unpack) against
+    numpy's float32 -> float64, which is exact: zeros, every float subnormal
+    exponent, normals, the largest value, infinities and NaN."""
+    d = tempfile.mkdtemp()
+    cu, exe = os.path.join(d, "w.cu"), os.path.join(d, "w")
+    with open(cu, "w") as f:
+        f.write(SRC_WIDEN)
+    r = subprocess.run([B.nvcc(), *B.ARCH, *B.FLAGS, "-DWD_TIMELINE", "-I", B.CSRC, cu, "-o", exe],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(r.stderr)
+    rng = np.random.default_rng(41)
+    bits = np.concatenate([
+        np.array([0, 0x80000000, 1, 0x80000001, 0x7FFFFF, 0x807FFFFF, 0x800000, 0x7F7FFFFF, 0xFF7FFFFF,
+                  0x7F800000, 0xFF800000, 0x7FC00000, 0x7FA00001], dtype=np.uint32),
+        (np.uint32(1) << np.arange(23, dtype=np.uint32)),                      # one subnormal per exponent
+        rng.integers(0, 1 << 23, 2000, dtype=np.uint32),                      # random subnormals
+        rng.integers(0, 1 << 32, 20000, dtype=np.uint64).astype(np.uint32),   # anything
+    ])
+    inp = "\n".join(f"{b:x}" for b in bits) + "\n"
+    out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
+    got = np.array([int(w, 16) for w in out], dtype=np.uint64).view(np.float64)
+    with np.errstate(invalid="ignore"):   # signalling NaNs among the random patterns
+        want = bits.view(np.float32).astype(np.float64)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), want[~nan].view(np.uint64))

@@ -82,7 +82,8 @@ S_OK, S_NOT_CONVERGED, S_BREAKDOWN, S_NONFINITE = 0, 4, 5, 6
 def stage_exe():
     d = tempfile.mkdtemp()
     cu, exe = os.path.join(d, "st.cu"), os.path.join(d, "st")
-    open(cu, "w").write(SRC)
+    with open(cu, "w") as f:
+        f.write(SRC)
     r = subprocess.run([B.nvcc(), *B.ARCH, *B.FLAGS, "-DWD_TIMELINE", "-I", B.CSRC, cu, "-o", exe],
                        capture_output=True, text=True)
     if r.returncode != 0:

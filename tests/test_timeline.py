@@ -29,7 +29,8 @@ def test_site_hash_matches_the_device_code():
            + "    return 0;\n}\n")
     with tempfile.TemporaryDirectory() as d:
         cu, exe = os.path.join(d, "h.cu"), os.path.join(d, "h")
-        open(cu, "w").write(src)
+        with open(cu, "w") as f:
+            f.write(src)
         r = subprocess.run([B.nvcc(), *B.ARCH, *B.FLAGS, "-DWD_TIMELINE", "-I", B.CSRC, cu, "-o", exe],
                            capture_output=True, text=True)
         if r.returncode != 0:
