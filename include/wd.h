@@ -456,6 +456,17 @@ int wd_precond_grad(wd_handle* h, int n, const float* v, const float* y, double 
 int wd_precond_train_step(wd_handle* h, int n, const float* v, const float* y, double mu, double lr, double* loss,
                           void* stream);
 
+/* The learned part under the names of its specified interface. wd_precond_load
+ * loads n = WD_PRECOND_FLOATS weights given as BF16 values (uint16 bit
+ * patterns, host memory, the flat layout above): each is widened exactly to
+ * FP32 and the result loaded as by wd_precond_set (Adam state reset).
+ * WD_ERR_INVALID_ARG for another n. wd_precond_train runs `steps` >= 1 calls
+ * of wd_precond_train_step on the same n samples; *loss (may be NULL)
+ * receives the loss before the last step. Errors as those calls. */
+int wd_precond_load(wd_handle* h, const void* weights_bf16, size_t n);
+int wd_precond_train(wd_handle* h, int steps, int n, const float* v, const float* y, double mu, double lr,
+                     double* loss, void* stream);
+
 /* Arithmetic throughput probe (not a feature of the paper): launches one
  * kernel on `stream` that runs `iters` steps of 8 independent fused
  * multiply-add chains per thread on the FP64 (bits = 64), FP32 (32) or

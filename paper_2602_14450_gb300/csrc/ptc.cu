@@ -904,6 +904,35 @@ extern "C" int wd_precond_train_step(wd_handle* h, int n, const float* v, const 
     return WD_OK;
 }
 
+// The same weights given as BF16 values in host memory: each widened exactly to FP32 (the BF16 bits are the
+// high half of the FP32 word) and loaded as the FP32 masters.
+extern "C" int wd_precond_load(wd_handle* h, const void* weights_bf16, size_t n) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!weights_bf16 || n != (size_t)PTC_FLOATS)
+        return fail(h, WD_ERR_INVALID_ARG, "wd_precond_load: n must be WD_PRECOND_FLOATS");
+    const unsigned short* b = static_cast<const unsigned short*>(weights_bf16);
+    std::vector<float> w(PTC_FLOATS);
+    for (size_t i = 0; i < n; ++i) {
+        const unsigned u = (unsigned)b[i] << 16;
+        std::memcpy(&w[i], &u, sizeof u);
+    }
+    return wd_precond_set(h, w.data(), WD_HOST);
+}
+
+// `steps` Adam steps on the same samples; *loss receives the loss before the last step.
+extern "C" int wd_precond_train(wd_handle* h, int steps, int n, const float* v, const float* y, double mu, double lr,
+                                double* loss, void* stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (steps < 1) return fail(h, WD_ERR_INVALID_ARG, "wd_precond_train: steps must be at least 1");
+    double l = 0.0;
+    for (int i = 0; i < steps; ++i) {
+        const int rc = wd_precond_train_step(h, n, v, y, mu, lr, &l, stream);
+        if (rc != WD_OK) return rc;
+    }
+    if (loss) *loss = l;
+    return WD_OK;
+}
+
 namespace wd {
 // Collapsed spin weights of the loaded network (device), or null when none are loaded.
 const float2* ptc_collapsed(wd_handle* h) {

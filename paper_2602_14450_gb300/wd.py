@@ -35,7 +35,7 @@ SYMBOLS = ["wd_create", "wd_destroy", "wd_set_gauge", "wd_gauge_unitarity", "wd_
            "wd_precond_get", "wd_precond_apply", "wd_precond_grad", "wd_precond_train_step", "wd_status_string",
            "wd_last_error", "wd_dd_set_partition", "wd_dd_face_bytes", "wd_dd_pack", "wd_dd_hop_interior",
            "wd_dd_hop_faces", "wd_vec_dot", "wd_vec_axpby", "wd_set_wait_limit", "wd_apply_batch",
-           "wd_set_rhs_per_thread", "wd_fma_probe", "wd_timeline_set"]
+           "wd_set_rhs_per_thread", "wd_fma_probe", "wd_timeline_set", "wd_precond_load", "wd_precond_train"]
 WD_MIXED_FP16_LEARNED = 5
 SCHEME["mixed_fp16_learned"] = WD_MIXED_FP16_LEARNED
 PRECOND_FLOATS = 6912
@@ -115,6 +115,8 @@ def lib():
         L.wd_precond_apply.argtypes = [vp, i, vp, vp, vp]
         L.wd_precond_grad.argtypes = [vp, i, vp, vp, d, vp, C.POINTER(d), vp]
         L.wd_precond_train_step.argtypes = [vp, i, vp, vp, d, d, C.POINTER(d), vp]
+        L.wd_precond_load.argtypes = [vp, vp, sz]
+        L.wd_precond_train.argtypes = [vp, i, i, vp, vp, d, d, C.POINTER(d), vp]
         L.wd_dd_set_partition.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.wd_dd_face_bytes.argtypes = [vp, i, i]
         L.wd_dd_face_bytes.restype = sz
@@ -336,6 +338,18 @@ class Lattice:
         loss = C.c_double()
         self._check(lib().wd_precond_train_step(self.h, int(v.shape[0]), _ptr(v), _ptr(y), float(mu), float(lr),
                                                 C.byref(loss), _stream(stream)), "wd_precond_train_step")
+        return loss.value
+
+    def precond_load(self, w_bf16):
+        """w_bf16: PRECOND_FLOATS BF16 weights (torch.bfloat16 or their int16 bit patterns), CPU."""
+        import torch
+        w = w_bf16.contiguous().view(torch.int16).cpu()
+        self._check(lib().wd_precond_load(self.h, _ptr(w), w.numel()), "wd_precond_load")
+
+    def precond_train(self, steps, v, y, mu, lr, stream=None):
+        loss = C.c_double()
+        self._check(lib().wd_precond_train(self.h, int(steps), int(v.shape[0]), _ptr(v), _ptr(y), float(mu),
+                                           float(lr), C.byref(loss), _stream(stream)), "wd_precond_train")
         return loss.value
 
     def solve_rhs(self, b, x, tol=1e-10, scheme="mixed_fp16", params=None, stream=None, check=True):

@@ -196,3 +196,21 @@ def test_training_is_reproducible():
         runs.append((losses, lat.precond_get()))
     assert runs[0][0] == runs[1][0]
     assert torch.equal(runs[0][1], runs[1][1])
+
+
+def test_specified_entry_points_load_and_train():
+    """wd_precond_load takes the weights as BF16 values and loads them widened
+    exactly to FP32 (the masters then equal the BF16 values); wd_precond_train
+    is that many wd_precond_train_step calls on the same samples, bit for bit."""
+    dims = (8, 8, 8, 8)
+    lat = lattice(synth.gauge_smeared(dims, seed=71), 0.12, dims)
+    v, y = learned.make_samples(lat, 2, seed=701)
+    wb = learned.initial_weights(5).to(torch.bfloat16)
+    lat.precond_load(wb)
+    assert torch.equal(lat.precond_get(), wb.to(torch.float32))
+    last = lat.precond_train(3, v, y, 1.0, 3e-3)
+    trained = lat.precond_get()
+    lat.precond_load(wb)
+    losses = [lat.precond_train_step(v, y, 1.0, 3e-3) for _ in range(3)]
+    assert last == losses[-1]
+    assert torch.equal(trained, lat.precond_get())
